@@ -1,0 +1,181 @@
+/*
+ * heat.h -- C ABI of the GB300 periodic 1D heat-stencil library (libheat.so).
+ *
+ * The operation (arXiv 2307.01117, Section 2 "Model problem"):
+ *   Eq. 1  u_t = alpha u_xx on a loop of length L with periodic boundary
+ *          u(t, x) = u(t, L + x);
+ *   Eq. 2  forward Euler on N grid points x_i = i h with second-order central
+ *          differences:  u'(x_i) = u(x_i) + r * ((u(x_{i-1}) - 2 u(x_i)) + u(x_{i+1})),
+ *          r = k * dt / dx^2  (k = alpha, dx = h; the printed "2h" denominator is
+ *          read as h^2, the value second-order differencing gives);
+ *   Section 2, parallel algorithm: the ring is split into np segments of nx
+ *          points; each segment is advanced by its own worker and ghost values
+ *          cross between neighbouring segments through single-producer
+ *          single-consumer queues.
+ *
+ * All arithmetic runs in the library's CUDA kernels (sm_103a).  Conventions for
+ * every call:
+ *   - Return value: HEAT_OK (0) or a negative heat_status code; heat_strerror()
+ *     names it.  A NULL context argument returns HEAT_EINVAL.
+ *   - Ownership: the context owns all device memory it allocates and frees it
+ *     in heat_destroy().  Pointers passed in are borrowed for the duration of
+ *     the call only.
+ *   - Layout: state arrays are in global ring order g = p*nx + j (partition p,
+ *     local index j), contiguous, N = np*nx elements.
+ *   - Streams: work is queued on the context's stream (its own non-blocking
+ *     stream unless heat_set_stream() names another).  heat_run() is
+ *     asynchronous; errors that arise on the device (a bounded wait that ran
+ *     out) are reported by the next synchronising call (heat_sync, heat_get,
+ *     heat_sum, heat_get_device).
+ *   - A context is not thread-safe: one host thread at a time.
+ */
+#ifndef HEAT_H
+#define HEAT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct heat_ctx heat_ctx; /* opaque, library-owned */
+
+/* Storage/arithmetic type of the ring state. */
+typedef enum {
+  HEAT_F64 = 0,  /* binary64 state; Eq. 2 in binary64 */
+  HEAT_F32C = 1  /* binary32 state; update in binary32 with a TwoSum-compensated
+                    correction carried within each temporal block (the paper
+                    has no reduced-precision form; this is the library's) */
+} heat_dtype;
+
+typedef enum {
+  HEAT_OK = 0,
+  HEAT_EINVAL = -1,   /* bad argument (sizes, non-finite or zero coefficients, NULL) */
+  HEAT_ENOMEM = -2,   /* device allocation failed */
+  HEAT_ECUDA = -3,    /* a CUDA runtime call failed (launch, copy, sync) */
+  HEAT_ETIMEOUT = -4, /* a bounded device wait on a neighbour's ghost ran out */
+  HEAT_ESTATE = -5,   /* call not valid in the context's state */
+  HEAT_ENOTSUP = -6   /* combination not supported (e.g. form for this dtype) */
+} heat_status;
+
+/* Kernel form used by heat_run().  All forms give bitwise the same result for
+ * HEAT_F64 with HEAT_ARITH_EXACT (the segmented algorithm of Section 2 computes
+ * every point with the same operation on the same operands as the unsegmented
+ * ring). */
+typedef enum {
+  HEAT_FORM_PLAIN = 0,   /* one global step per launch; ghost exchange implicit
+                            through the launch boundary (Section 3.1's
+                            synchronous, unsegmented variant) */
+  HEAT_FORM_PERSIST = 1, /* one persistent launch; each CTA owns a segment and
+                            swaps ghost values with its neighbours through
+                            device-memory flag queues (Section 2's SPSC queues) */
+  HEAT_FORM_TBLOCK = 2,  /* temporal blocking: T steps per shared-memory tile */
+  HEAT_FORM_AUTO = 3     /* library picks by ring size and dtype */
+} heat_form;
+
+/* Rounding reading of Eq. 2 for HEAT_F64 (the paper states no order). */
+typedef enum {
+  HEAT_ARITH_EXACT = 0, /* v = u + r*((ul - 2u) + ur), each operation rounded once
+                           to nearest-even, left to right (bit-exact with a plain
+                           C evaluation without contraction) */
+  HEAT_ARITH_FMA = 1    /* v = fma(r, (ul - 2u) + ur, u): one rounding fewer */
+} heat_arith;
+
+/* Create a ring of np partitions x nx points with Eq. 2 coefficient
+ * r = (k*dt)/(dx*dx), computed once on the host in binary64.
+ *   out   receives the new context (set to NULL on failure).
+ *   nx>=1, np>=1, nx*np must not overflow int64; k, dt, dx finite, dx != 0.
+ *   r > 1/2 is accepted (explicit Euler is then unstable; not an error).
+ * The state is zero until heat_set().  Returns HEAT_EINVAL, HEAT_ENOMEM or
+ * HEAT_ECUDA on failure (nothing is leaked). */
+int heat_create(heat_ctx **out, int64_t nx, int32_t np, double k, double dt, double dx,
+                heat_dtype dtype);
+
+/* Free every device resource of the context (synchronises its stream).  NULL is
+ * a no-op. */
+void heat_destroy(heat_ctx *c);
+
+/* Load the state from host memory: host_u holds n = np*nx binary64 values in
+ * global order (Section 2's initial condition u(0, x_i) is the caller's).  For
+ * HEAT_F32C each value is rounded to nearest binary32 on the device.  Resets the
+ * step counter to 0.  Synchronous.  n != np*nx -> HEAT_EINVAL. */
+int heat_set(heat_ctx *c, const double *host_u, int64_t n);
+
+/* Read the state into host memory (n = np*nx binary64 values; binary32 state is
+ * widened exactly).  Synchronises the context's stream first and reports a
+ * pending device error, if any, instead of copying. */
+int heat_get(heat_ctx *c, double *host_u, int64_t n);
+
+/* Same as heat_set / heat_get with a device pointer (binary64, n elements,
+ * 8-byte aligned) instead of a host pointer; the copy is queued on the
+ * context's stream (heat_set_device returns without waiting; heat_get_device
+ * waits for the stream). */
+int heat_set_device(heat_ctx *c, const double *dev_u, int64_t n);
+int heat_get_device(heat_ctx *c, double *dev_u, int64_t n);
+
+/* Advance the state by nt >= 0 steps of Eq. 2 with the current form and
+ * arithmetic.  Asynchronous on the context's stream; returns HEAT_EINVAL for
+ * nt < 0, HEAT_ESTATE if a device error is pending, HEAT_ECUDA if a launch
+ * fails.  Errors found on the device during the run surface at the next
+ * synchronising call. */
+int heat_run(heat_ctx *c, int64_t nt);
+
+/* Wait for the context's stream and report a pending device error
+ * (HEAT_ETIMEOUT) or HEAT_OK.  The pending error is cleared by heat_set(). */
+int heat_sync(heat_ctx *c);
+
+/* Queue subsequent work on cuda_stream (a cudaStream_t, e.g. the handle of a
+ * torch.cuda.Stream); NULL restores the context's own stream. */
+int heat_set_stream(heat_ctx *c, void *cuda_stream);
+
+/* Select the kernel form and, for HEAT_FORM_TBLOCK, the temporal block depth
+ * T (1..64; 0 = library default).  T is ignored by the other forms. */
+int heat_set_form(heat_ctx *c, int form, int T);
+
+/* Segmentation of the persistent forms: 0 = library default (near-equal
+ * segments, one per co-resident CTA, interior boundaries on 64-point tiles);
+ * -1 = one segment per partition of nx points, as in the paper's algorithm, when
+ * np CTAs can be co-resident (else the default); n > 0 = at most n near-equal
+ * segments.  The result does not depend on this choice. */
+int heat_set_segments(heat_ctx *c, int segments);
+
+/* Select the rounding reading for HEAT_F64 (heat_arith).  HEAT_F32C ignores it. */
+int heat_set_arith(heat_ctx *c, int arith);
+
+/* Deterministic FP64 sum of the state into *out (host pointer): a fixed-shape
+ * tree, so the value does not depend on timing or on the GPU.  It is the conservation
+ * diagnostic: sum(u) is invariant under Eq. 2 on the periodic ring.
+ * Synchronous. */
+int heat_sum(heat_ctx *c, double *out);
+
+/* Number of steps applied since the last heat_set (the checkpoint counter:
+ * heat_get + this count is a checkpoint; heat_set restores). */
+int heat_steps(const heat_ctx *c, int64_t *out);
+
+/* Ring geometry and the coefficient actually used. */
+int heat_info(const heat_ctx *c, int64_t *nx, int32_t *np, double *r, int *dtype);
+
+/* Device pointer of the current state buffer (dtype elements, global order).
+ * Borrowed: valid until the next heat_run/heat_set/heat_destroy. */
+int heat_state_ptr(heat_ctx *c, void **dev_ptr);
+
+/* Upper bound, in nanoseconds, on any single device wait for a neighbour's
+ * ghost value in the persistent forms (default 2e9).  A wait that runs out
+ * stops the run and reports HEAT_ETIMEOUT. */
+int heat_set_wait_limit(heat_ctx *c, int64_t ns);
+
+/* Test hook (host-side fault injection): in the next persistent run, the CTA
+ * owning segment `segment` stops publishing its edge values from step
+ * `from_step` on, so its neighbours' bounded waits run out and the run ends with
+ * HEAT_ETIMEOUT while every kernel still returns normally.  segment < 0
+ * disables the hook.  No GPU fault or trap is involved. */
+int heat_inject_stall(heat_ctx *c, int32_t segment, int64_t from_step);
+
+/* Static text for a status code. */
+const char *heat_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HEAT_H */

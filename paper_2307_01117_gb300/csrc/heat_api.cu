@@ -1,0 +1,309 @@
+// heat_api.cu -- the C ABI of include/heat.h: context lifetime, argument
+// validation, state transfer and dispatch to the kernel forms.
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include "heat_internal.cuh"
+
+using heat::DevStatus;
+
+namespace {
+
+constexpr int64_t kStageElems = int64_t(1) << 22;  // binary64 staging chunk for HEAT_F32C transfers (32 MiB)
+
+bool is_finite(double x) { return isfinite(x) != 0; }
+
+void free_ctx(heat_ctx *c) {
+  if (!c) return;
+  if (c->own_stream) cudaStreamSynchronize(c->own_stream);
+  if (c->stream && c->stream != c->own_stream) cudaStreamSynchronize(c->stream);
+  for (int i = 0; i < 2; ++i)
+    if (c->buf[i]) cudaFree(c->buf[i]);
+  if (c->dstat) cudaFree(c->dstat);
+  if (c->hstat) cudaFreeHost(c->hstat);
+  if (c->mbox) cudaFree(c->mbox);
+  if (c->seg_start) cudaFree(c->seg_start);
+  if (c->partials) cudaFree(c->partials);
+  if (c->hsum) cudaFreeHost(c->hsum);
+  if (c->own_stream) cudaStreamDestroy(c->own_stream);
+  free(c);
+}
+
+// Wait for the stream, then fold the device status word into the sticky host
+// error.  Returns the sticky error (HEAT_OK if none).
+int sync_status(heat_ctx *c) {
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return HEAT_ECUDA;
+  if (cudaMemcpyAsync(c->hstat, c->dstat, sizeof(DevStatus), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess)
+    return HEAT_ECUDA;
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return HEAT_ECUDA;
+  if (c->hstat->code != HEAT_OK && c->host_error == HEAT_OK) c->host_error = c->hstat->code;
+  return c->host_error;
+}
+
+int reset_status(heat_ctx *c) {
+  c->host_error = HEAT_OK;
+  return heat::cuda_status(cudaMemsetAsync(c->dstat, 0, sizeof(DevStatus), c->stream));
+}
+
+}  // namespace
+
+extern "C" {
+
+int heat_create(heat_ctx **out, int64_t nx, int32_t np, double k, double dt, double dx, heat_dtype dtype) {
+  if (!out) return HEAT_EINVAL;
+  *out = nullptr;
+  if (nx < 1 || np < 1) return HEAT_EINVAL;
+  if (nx > INT64_MAX / np) return HEAT_EINVAL;
+  if (!is_finite(k) || !is_finite(dt) || !is_finite(dx) || dx == 0.0) return HEAT_EINVAL;
+  if (dtype != HEAT_F64 && dtype != HEAT_F32C) return HEAT_EINVAL;
+  const int64_t N = nx * (int64_t)np;
+  const size_t elem = dtype == HEAT_F64 ? sizeof(double) : sizeof(float);
+  if ((uint64_t)N > (uint64_t)(SIZE_MAX / 2 / elem)) return HEAT_EINVAL;
+  const double r = (k * dt) / (dx * dx);
+  if (!is_finite(r)) return HEAT_EINVAL;
+
+  heat_ctx *c = (heat_ctx *)calloc(1, sizeof(heat_ctx));
+  if (!c) return HEAT_ENOMEM;
+  c->geo.nx = nx;
+  c->geo.np = np;
+  c->geo.N = N;
+  c->r = r;
+  c->rf = (float)r;
+  c->dtype = dtype;
+  c->elem = elem;
+  c->form = HEAT_FORM_AUTO;
+  c->T = 0;
+  c->arith = HEAT_ARITH_EXACT;
+  c->wait_ns = 2000000000LL;
+  c->inj_segment = -1;
+  c->inj_step = 0;
+  int rc = HEAT_OK;
+  if (cudaGetDevice(&c->device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess) {
+    cudaGetLastError();
+    free(c);
+    return HEAT_ECUDA;
+  }
+  if (cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    free(c);
+    return HEAT_ECUDA;
+  }
+  c->stream = c->own_stream;
+  for (int i = 0; i < 2 && rc == HEAT_OK; ++i)
+    if (cudaMalloc(&c->buf[i], (size_t)N * elem) != cudaSuccess) rc = HEAT_ENOMEM;
+  if (rc == HEAT_OK && cudaMalloc((void **)&c->dstat, sizeof(DevStatus)) != cudaSuccess) rc = HEAT_ENOMEM;
+  if (rc == HEAT_OK && cudaMallocHost((void **)&c->hstat, sizeof(DevStatus)) != cudaSuccess) rc = HEAT_ENOMEM;
+  if (rc == HEAT_OK && cudaMalloc((void **)&c->partials, sizeof(double) * (heat::kSumBlocks + 1)) != cudaSuccess)
+    rc = HEAT_ENOMEM;
+  if (rc == HEAT_OK && cudaMallocHost((void **)&c->hsum, sizeof(double)) != cudaSuccess) rc = HEAT_ENOMEM;
+  if (rc == HEAT_OK) {
+    for (int i = 0; i < 2 && rc == HEAT_OK; ++i)
+      if (cudaMemsetAsync(c->buf[i], 0, (size_t)N * elem, c->stream) != cudaSuccess) rc = HEAT_ECUDA;
+    if (rc == HEAT_OK) rc = reset_status(c);
+    if (rc == HEAT_OK && cudaStreamSynchronize(c->stream) != cudaSuccess) rc = HEAT_ECUDA;
+  }
+  if (rc != HEAT_OK) {
+    cudaGetLastError();
+    free_ctx(c);
+    return rc;
+  }
+  *out = c;
+  return HEAT_OK;
+}
+
+void heat_destroy(heat_ctx *c) { free_ctx(c); }
+
+// Copies n binary64 values (host or device source) into the state buffer.
+static int load_state(heat_ctx *c, const double *src, int64_t n, cudaMemcpyKind kind) {
+  if (!c || !src) return HEAT_EINVAL;
+  if (n != c->geo.N) return HEAT_EINVAL;
+  int rc = reset_status(c);
+  if (rc != HEAT_OK) return rc;
+  void *dst = c->buf[c->cur];
+  if (c->dtype == HEAT_F64) {
+    if (cudaMemcpyAsync(dst, src, (size_t)n * sizeof(double), kind, c->stream) != cudaSuccess) return HEAT_ECUDA;
+  } else if (kind == cudaMemcpyDeviceToDevice) {
+    rc = heat::convert_f64_to_state(c, src, dst, n);
+    if (rc != HEAT_OK) return rc;
+  } else {
+    // binary64 input does not fit the binary32 buffers: stage it through a
+    // transient device chunk and round each chunk on the device
+    double *stage = nullptr;
+    const int64_t chunk = n < kStageElems ? n : kStageElems;
+    if (cudaMalloc((void **)&stage, (size_t)chunk * sizeof(double)) != cudaSuccess) return HEAT_ENOMEM;
+    for (int64_t off = 0; off < n && rc == HEAT_OK; off += chunk) {
+      const int64_t m = n - off < chunk ? n - off : chunk;
+      if (cudaMemcpyAsync(stage, src + off, (size_t)m * sizeof(double), kind, c->stream) != cudaSuccess) rc = HEAT_ECUDA;
+      if (rc == HEAT_OK) rc = heat::convert_f64_to_state(c, stage, (float *)dst + off, m);
+      if (rc == HEAT_OK && cudaStreamSynchronize(c->stream) != cudaSuccess) rc = HEAT_ECUDA;
+    }
+    cudaStreamSynchronize(c->stream);
+    cudaFree(stage);
+    if (rc != HEAT_OK) return rc;
+  }
+  c->steps = 0;
+  return HEAT_OK;
+}
+
+int heat_set(heat_ctx *c, const double *host_u, int64_t n) {
+  int rc = load_state(c, host_u, n, cudaMemcpyHostToDevice);
+  if (rc != HEAT_OK) return rc;
+  return cudaStreamSynchronize(c->stream) == cudaSuccess ? HEAT_OK : HEAT_ECUDA;
+}
+
+int heat_set_device(heat_ctx *c, const double *dev_u, int64_t n) {
+  return load_state(c, dev_u, n, cudaMemcpyDeviceToDevice);
+}
+
+static int store_state(heat_ctx *c, double *dst, int64_t n, cudaMemcpyKind kind) {
+  if (!c || !dst) return HEAT_EINVAL;
+  if (n != c->geo.N) return HEAT_EINVAL;
+  int rc = sync_status(c);
+  if (rc != HEAT_OK) return rc;
+  const void *src = c->buf[c->cur];
+  if (c->dtype == HEAT_F64) {
+    if (cudaMemcpyAsync(dst, src, (size_t)n * sizeof(double), kind, c->stream) != cudaSuccess) return HEAT_ECUDA;
+  } else if (kind == cudaMemcpyDeviceToDevice) {
+    rc = heat::convert_state_to_f64(c, src, dst, n);
+    if (rc != HEAT_OK) return rc;
+  } else {
+    double *stage = nullptr;
+    const int64_t chunk = n < kStageElems ? n : kStageElems;
+    if (cudaMalloc((void **)&stage, (size_t)chunk * sizeof(double)) != cudaSuccess) return HEAT_ENOMEM;
+    for (int64_t off = 0; off < n && rc == HEAT_OK; off += chunk) {
+      const int64_t m = n - off < chunk ? n - off : chunk;
+      rc = heat::convert_state_to_f64(c, (const float *)src + off, stage, m);
+      if (rc == HEAT_OK && cudaMemcpyAsync(dst + off, stage, (size_t)m * sizeof(double), kind, c->stream) != cudaSuccess)
+        rc = HEAT_ECUDA;
+      if (rc == HEAT_OK && cudaStreamSynchronize(c->stream) != cudaSuccess) rc = HEAT_ECUDA;
+    }
+    cudaStreamSynchronize(c->stream);
+    cudaFree(stage);
+    if (rc != HEAT_OK) return rc;
+  }
+  return cudaStreamSynchronize(c->stream) == cudaSuccess ? HEAT_OK : HEAT_ECUDA;
+}
+
+int heat_get(heat_ctx *c, double *host_u, int64_t n) { return store_state(c, host_u, n, cudaMemcpyDeviceToHost); }
+
+int heat_get_device(heat_ctx *c, double *dev_u, int64_t n) { return store_state(c, dev_u, n, cudaMemcpyDeviceToDevice); }
+
+int heat_run(heat_ctx *c, int64_t nt) {
+  if (!c || nt < 0) return HEAT_EINVAL;
+  if (c->host_error != HEAT_OK) return HEAT_ESTATE;
+  if (nt == 0) return HEAT_OK;
+  int form = c->form;
+  if (form == HEAT_FORM_AUTO) form = HEAT_FORM_PLAIN;
+  switch (form) {
+    case HEAT_FORM_PLAIN: return heat::run_plain(c, nt);
+    case HEAT_FORM_PERSIST: return heat::run_persist(c, nt);
+    case HEAT_FORM_TBLOCK: return heat::run_tblock(c, nt);
+    default: return HEAT_EINVAL;
+  }
+}
+
+int heat_sync(heat_ctx *c) {
+  if (!c) return HEAT_EINVAL;
+  return sync_status(c);
+}
+
+int heat_set_stream(heat_ctx *c, void *cuda_stream) {
+  if (!c) return HEAT_EINVAL;
+  cudaStream_t next = cuda_stream ? (cudaStream_t)cuda_stream : c->own_stream;
+  if (next == c->stream) return HEAT_OK;
+  // keep queued work ordered across the switch
+  cudaEvent_t ev;
+  if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) return HEAT_ECUDA;
+  int rc = HEAT_OK;
+  if (cudaEventRecord(ev, c->stream) != cudaSuccess || cudaStreamWaitEvent(next, ev, 0) != cudaSuccess) rc = HEAT_ECUDA;
+  cudaEventDestroy(ev);
+  if (rc == HEAT_OK) c->stream = next;
+  return rc;
+}
+
+int heat_set_form(heat_ctx *c, int form, int T) {
+  if (!c) return HEAT_EINVAL;
+  if (form < HEAT_FORM_PLAIN || form > HEAT_FORM_AUTO) return HEAT_EINVAL;
+  if (T < 0 || T > heat::kMaxT) return HEAT_EINVAL;
+  c->form = form;
+  c->T = T;
+  return HEAT_OK;
+}
+
+int heat_set_segments(heat_ctx *c, int segments) {
+  if (!c || segments < -1) return HEAT_EINVAL;
+  c->segments = segments;
+  return HEAT_OK;
+}
+
+int heat_set_arith(heat_ctx *c, int arith) {
+  if (!c) return HEAT_EINVAL;
+  if (arith != HEAT_ARITH_EXACT && arith != HEAT_ARITH_FMA) return HEAT_EINVAL;
+  c->arith = arith;
+  return HEAT_OK;
+}
+
+int heat_sum(heat_ctx *c, double *out) {
+  if (!c || !out) return HEAT_EINVAL;
+  int rc = sync_status(c);
+  if (rc != HEAT_OK) return rc;
+  rc = heat::sum_state(c, c->partials + heat::kSumBlocks);
+  if (rc != HEAT_OK) return rc;
+  if (cudaMemcpyAsync(c->hsum, c->partials + heat::kSumBlocks, sizeof(double), cudaMemcpyDeviceToHost, c->stream) !=
+      cudaSuccess)
+    return HEAT_ECUDA;
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return HEAT_ECUDA;
+  *out = *c->hsum;
+  return HEAT_OK;
+}
+
+int heat_steps(const heat_ctx *c, int64_t *out) {
+  if (!c || !out) return HEAT_EINVAL;
+  *out = c->steps;
+  return HEAT_OK;
+}
+
+int heat_info(const heat_ctx *c, int64_t *nx, int32_t *np, double *r, int *dtype) {
+  if (!c) return HEAT_EINVAL;
+  if (nx) *nx = c->geo.nx;
+  if (np) *np = c->geo.np;
+  if (r) *r = c->r;
+  if (dtype) *dtype = (int)c->dtype;
+  return HEAT_OK;
+}
+
+int heat_state_ptr(heat_ctx *c, void **dev_ptr) {
+  if (!c || !dev_ptr) return HEAT_EINVAL;
+  *dev_ptr = c->buf[c->cur];
+  return HEAT_OK;
+}
+
+int heat_set_wait_limit(heat_ctx *c, int64_t ns) {
+  if (!c || ns < 1) return HEAT_EINVAL;
+  c->wait_ns = ns;
+  return HEAT_OK;
+}
+
+int heat_inject_stall(heat_ctx *c, int32_t segment, int64_t from_step) {
+  if (!c || from_step < 0) return HEAT_EINVAL;
+  c->inj_segment = segment < 0 ? -1 : segment;
+  c->inj_step = from_step;
+  return HEAT_OK;
+}
+
+const char *heat_strerror(int code) {
+  switch (code) {
+    case HEAT_OK: return "ok";
+    case HEAT_EINVAL: return "invalid argument";
+    case HEAT_ENOMEM: return "device allocation failed";
+    case HEAT_ECUDA: return "CUDA runtime error";
+    case HEAT_ETIMEOUT: return "bounded wait for a neighbour's ghost value ran out";
+    case HEAT_ESTATE: return "a device error is pending; reload the state with heat_set";
+    case HEAT_ENOTSUP: return "combination not supported";
+    default: return "unknown status";
+  }
+}
+
+}  // extern "C"

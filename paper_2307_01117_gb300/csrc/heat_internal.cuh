@@ -1,0 +1,92 @@
+// heat_internal.cuh -- context layout and launcher interfaces shared by the
+// translation units of libheat.so.  Not part of the public ABI (include/heat.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/heat.h"
+
+namespace heat {
+
+// Largest temporal block depth (steps per tile load) the kernels accept.
+constexpr int kMaxT = 64;
+
+// One inbound ghost mailbox of the persistent forms (the GPU form of the
+// single-producer single-consumer queue of Section 2).  The producer writes
+// val[slot][0..T) and then stores seq with release semantics; the consumer
+// acquires seq and reads.  Two slots suffice because neighbours never drift
+// more than one step (block) apart: a producer can only overwrite slot s%2 with
+// the values of step s+2 after it has acquired the consumer's step-(s+1)
+// publication, which the consumer makes after reading slot s%2.
+struct __align__(128) Mailbox {
+  unsigned long long seq;
+  unsigned long long pad[15];
+  double val[2][kMaxT];
+};
+
+// Device-side status, written by kernels, read by the host at sync points.
+struct DevStatus {
+  int code;            // HEAT_OK or HEAT_ETIMEOUT (first error wins)
+  int segment;         // segment whose wait ran out
+  long long step;      // step at which it ran out
+  int abort;           // set by the first CTA that gives up; others stop waiting
+  int pad;
+};
+
+struct Geometry {
+  int64_t nx;
+  int32_t np;
+  int64_t N;
+};
+
+}  // namespace heat
+
+struct heat_ctx {
+  heat::Geometry geo;
+  double r;          // k*dt/(dx*dx), binary64
+  float rf;          // (float)r for HEAT_F32C
+  heat_dtype dtype;
+  int device;
+  int sms;
+  size_t elem;       // bytes per state element
+  void *buf[2];      // double-buffered state, global order
+  int cur;           // index of the buffer holding the current state
+  cudaStream_t own_stream;
+  cudaStream_t stream;
+  int form;
+  int T;
+  int arith;
+  int64_t steps;
+  int host_error;                // sticky device error seen at the last sync
+  heat::DevStatus *dstat;        // device
+  heat::DevStatus *hstat;        // pinned host mirror
+  heat::Mailbox *mbox;           // 2 per segment (in_left, in_right), device
+  int64_t *seg_start;            // segment table (S+1 entries), device
+  int mbox_segments;             // capacity of mbox / seg_start
+  int segments;                  // persistent segmentation: 0 auto, -1 one per partition, >0 count
+  int last_segments;             // segments used by the last persistent run
+  double *partials;              // reduction scratch, device
+  double *hsum;                  // pinned host word for heat_sum
+  int64_t wait_ns;
+  int32_t inj_segment;
+  int64_t inj_step;
+};
+
+namespace heat {
+
+// Launchers (each queues work on c->stream and returns a heat_status).
+int run_plain(heat_ctx *c, int64_t nt);
+int run_persist(heat_ctx *c, int64_t nt);
+int run_tblock(heat_ctx *c, int64_t nt);
+int sum_state(heat_ctx *c, double *out);
+int convert_f64_to_state(heat_ctx *c, const double *dev_src, void *dev_dst, int64_t n);
+int convert_state_to_f64(heat_ctx *c, const void *dev_src, double *dev_dst, int64_t n);
+
+// Number of reduction partials heat_sum uses (fixed, so the tree is fixed).
+constexpr int kSumBlocks = 1024;
+constexpr int kSumThreads = 256;
+
+inline int cuda_status(cudaError_t e) { return e == cudaSuccess ? HEAT_OK : HEAT_ECUDA; }
+
+}  // namespace heat

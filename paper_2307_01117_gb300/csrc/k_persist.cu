@@ -1,0 +1,307 @@
+// k_persist.cu -- form HEAT_FORM_PERSIST: one persistent, co-resident
+// (cooperative) launch runs all nt steps.  The ring is cut into S segments
+// (Section 2: "each thread of execution sequentially applies Eq. 2 on a local
+// segment"); CTA c owns segments c, c + grid, ...  Ghost values cross between
+// neighbouring segments through device-memory mailboxes -- the GPU form of the
+// paper's single-producer single-consumer queues:
+//
+//   producer, after finishing step s of its segment:
+//       write the segment's first value into the left neighbour's in_right
+//       mailbox and its last value into the right neighbour's in_left mailbox,
+//       slot (s+1) % 2; fence; st.release.gpu seq = s + 2
+//   consumer, before step s:
+//       ld.acquire.gpu seq until seq >= s + 1 (bounded), read slot s % 2
+//
+// Every wait is bounded by an iteration cap and a %globaltimer deadline; a wait
+// that runs out records HEAT_ETIMEOUT in the device status word, raises the
+// shared abort flag (so the other CTAs stop waiting) and the kernel returns
+// normally.  Within a segment, points are processed as in the plain form (64-
+// point warp tiles, 16-byte vectors, shuffles for in-tile neighbours).
+#include "heat_internal.cuh"
+#include "stencil_ops.cuh"
+
+namespace heat {
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kPersistThreads = 512;
+constexpr long long kMaxSpins = 1LL << 26;  // backstop if the timer never advances
+
+__device__ __forceinline__ unsigned long long ld_acquire(const unsigned long long *p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void st_release(unsigned long long *p, unsigned long long v) {
+  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ int ld_volatile(const int *p) { return *(const volatile int *)p; }
+
+struct PersistArgs {
+  void *ua;               // state at time 0 on entry
+  void *ub;               // other buffer
+  int64_t N;
+  double r;
+  float rf;
+  int64_t nt;
+  const int64_t *seg;     // S + 1 boundaries, seg[0] = 0, seg[S] = N
+  int S;
+  Mailbox *mb;            // mb[2i] = in_left of segment i, mb[2i+1] = in_right
+  DevStatus *st;
+  long long wait_ns;
+  int inj_seg;
+  long long inj_step;
+};
+
+// Bounded wait until *seq >= target.  Returns false when the deadline passed or
+// another CTA already gave up (abort); the first CTA to give up records where.
+__device__ bool wait_seq(const PersistArgs &a, const unsigned long long *seq, unsigned long long target, int segment,
+                         long long step) {
+  if (ld_acquire(seq) >= target) return true;
+  const unsigned long long deadline = globaltimer_ns() + (unsigned long long)a.wait_ns;
+  unsigned ns = 32;
+  for (long long spin = 0; spin < kMaxSpins; ++spin) {
+    if (ld_acquire(seq) >= target) return true;
+    if (ld_volatile(&a.st->abort)) return false;
+    if (globaltimer_ns() > deadline) break;
+    __nanosleep(ns);
+    if (ns < 1024) ns <<= 1;
+  }
+  if (atomicCAS(&a.st->code, HEAT_OK, HEAT_ETIMEOUT) == HEAT_OK) {
+    a.st->segment = segment;
+    a.st->step = step;
+  }
+  atomicExch(&a.st->abort, 1);
+  return false;
+}
+
+template <int MODE>
+struct Elem;
+template <>
+struct Elem<0> {
+  using T = double;
+  using V = double2;
+  static __device__ __forceinline__ double upd(double l, double c, double r_, double r, float) {
+    return eq2_exact(l, c, r_, r);
+  }
+};
+template <>
+struct Elem<1> {
+  using T = double;
+  using V = double2;
+  static __device__ __forceinline__ double upd(double l, double c, double r_, double r, float) {
+    return eq2_fma(l, c, r_, r);
+  }
+};
+template <>
+struct Elem<2> {
+  using T = float;
+  using V = float2;
+  static __device__ __forceinline__ float upd(float l, float c, float r_, double, float rf) {
+    float hn, ln;
+    eq2_f32c(l, c, r_, 0.0f, 0.0f, 0.0f, rf, hn, ln);
+    return f32c_store(hn, ln);
+  }
+};
+
+// One step over the segment [lo, hi) of src into dst with the given ghosts.
+// src was written earlier in this same launch, so it is read with plain
+// L2-cached loads (never the read-only non-coherent path).
+template <int MODE>
+__device__ __forceinline__ void step_segment(const typename Elem<MODE>::T *src, typename Elem<MODE>::T *dst,
+                                             int64_t lo, int64_t hi,
+                                             typename Elem<MODE>::T gl, typename Elem<MODE>::T gr, double r,
+                                             float rf) {
+  using E = Elem<MODE>;
+  using T = typename E::T;
+  using V = typename E::V;
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  const int nwarps = blockDim.x >> 5;
+  const int64_t t0 = lo >> 6;
+  const int64_t t1 = (hi + 63) >> 6;
+  for (int64_t t = t0 + warp; t < t1; t += nwarps) {
+    const int64_t b = t << 6;
+    if (b >= lo && b + 64 <= hi) {
+      const V x = __ldcg(reinterpret_cast<const V *>(src + b) + lane);
+      T left = __shfl_up_sync(kFull, x.y, 1);
+      T right = __shfl_down_sync(kFull, x.x, 1);
+      if (lane == 0) left = b == lo ? gl : __ldcg(src + b - 1);
+      if (lane == 31) right = b + 64 == hi ? gr : __ldcg(src + b + 64);
+      V y;
+      y.x = E::upd(left, x.x, x.y, r, rf);
+      y.y = E::upd(x.x, x.y, right, r, rf);
+      reinterpret_cast<V *>(dst + b)[lane] = y;
+    } else {
+      for (int j = lane; j < 64; j += 32) {
+        const int64_t g = b + j;
+        if (g < lo || g >= hi) continue;
+        const T ul = g == lo ? gl : __ldcg(src + g - 1);
+        const T ur = g == hi - 1 ? gr : __ldcg(src + g + 1);
+        dst[g] = E::upd(ul, __ldcg(src + g), ur, r, rf);
+      }
+    }
+  }
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(kPersistThreads) k_persist(PersistArgs a) {
+  using T = typename Elem<MODE>::T;
+  __shared__ T ghost[2];
+  __shared__ int stop;
+  const T *src = (const T *)a.ua;
+  T *dst = (T *)a.ub;
+  const int S = a.S;
+
+  // publish the time-0 edge values of every owned segment
+  if (threadIdx.x == 0) {
+    for (int i = blockIdx.x; i < S; i += gridDim.x) {
+      if (i == a.inj_seg && a.inj_step <= 0) continue;
+      const int left = i == 0 ? S - 1 : i - 1, right = i == S - 1 ? 0 : i + 1;
+      a.mb[2 * left + 1].val[0][0] = (double)__ldcg(src + a.seg[i]);
+      a.mb[2 * right].val[0][0] = (double)__ldcg(src + a.seg[i + 1] - 1);
+      __threadfence();
+      st_release(&a.mb[2 * left + 1].seq, 1ull);
+      st_release(&a.mb[2 * right].seq, 1ull);
+    }
+  }
+
+  for (long long s = 0; s < a.nt; ++s) {
+    for (int i = blockIdx.x; i < S; i += gridDim.x) {
+      const int64_t lo = a.seg[i], hi = a.seg[i + 1];
+      if (threadIdx.x == 0) {
+        const bool ok = wait_seq(a, &a.mb[2 * i].seq, (unsigned long long)s + 1, i, s) &&
+                        wait_seq(a, &a.mb[2 * i + 1].seq, (unsigned long long)s + 1, i, s);
+        if (ok) {
+          ghost[0] = (T)(*(volatile double *)&a.mb[2 * i].val[s & 1][0]);
+          ghost[1] = (T)(*(volatile double *)&a.mb[2 * i + 1].val[s & 1][0]);
+        }
+        stop = ok ? 0 : 1;
+      }
+      __syncthreads();
+      if (stop) return;  // uniform across the CTA
+      step_segment<MODE>(src, dst, lo, hi, ghost[0], ghost[1], a.r, a.rf);
+      __syncthreads();
+      if (threadIdx.x == 0 && !(i == a.inj_seg && s + 1 >= a.inj_step)) {
+        const int left = i == 0 ? S - 1 : i - 1, right = i == S - 1 ? 0 : i + 1;
+        const int slot = (int)((s + 1) & 1);
+        a.mb[2 * left + 1].val[slot][0] = (double)__ldcg(dst + lo);
+        a.mb[2 * right].val[slot][0] = (double)__ldcg(dst + hi - 1);
+        __threadfence();
+        st_release(&a.mb[2 * left + 1].seq, (unsigned long long)s + 2);
+        st_release(&a.mb[2 * right].seq, (unsigned long long)s + 2);
+      }
+    }
+    const T *t = src;
+    src = dst;
+    dst = (T *)t;
+  }
+}
+
+template <int MODE>
+int launch(heat_ctx *c, PersistArgs &a, int grid) {
+  void *params[] = {&a};
+  const cudaError_t e = cudaLaunchCooperativeKernel((const void *)k_persist<MODE>, dim3(grid), dim3(kPersistThreads),
+                                                    params, 0, c->stream);
+  return e == cudaSuccess ? HEAT_OK : HEAT_ECUDA;
+}
+
+template <int MODE>
+int max_resident(heat_ctx *c) {
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_persist<MODE>, kPersistThreads, 0) != cudaSuccess)
+    return 0;
+  return per_sm * c->sms;
+}
+
+}  // namespace
+
+// Builds the segment table (S+1 boundaries) on the host and uploads it; makes
+// sure the mailbox area holds 2*S mailboxes.
+int prepare_segments(heat_ctx *c, int S, const int64_t *bounds) {
+  if (S > c->mbox_segments) {
+    if (c->mbox) cudaFree(c->mbox);
+    if (c->seg_start) cudaFree(c->seg_start);
+    c->mbox = nullptr;
+    c->seg_start = nullptr;
+    c->mbox_segments = 0;
+    if (cudaMalloc((void **)&c->mbox, sizeof(Mailbox) * 2 * (size_t)S) != cudaSuccess) return HEAT_ENOMEM;
+    if (cudaMalloc((void **)&c->seg_start, sizeof(int64_t) * (size_t)(S + 1)) != cudaSuccess) return HEAT_ENOMEM;
+    c->mbox_segments = S;
+  }
+  if (cudaMemcpyAsync(c->seg_start, bounds, sizeof(int64_t) * (size_t)(S + 1), cudaMemcpyHostToDevice, c->stream) !=
+      cudaSuccess)
+    return HEAT_ECUDA;
+  // fresh sequence numbers for this run (the kernel republishes time-0 edges)
+  if (cudaMemsetAsync(c->mbox, 0, sizeof(Mailbox) * 2 * (size_t)S, c->stream) != cudaSuccess) return HEAT_ECUDA;
+  // the bounds array is a host temporary: make the copy complete before returning
+  return cudaStreamSynchronize(c->stream) == cudaSuccess ? HEAT_OK : HEAT_ECUDA;
+}
+
+// Segment boundaries: one segment per partition when requested (and the
+// partitions fit the co-resident CTAs), else `want` near-equal segments whose
+// interior boundaries fall on 64-point tiles.
+int segment_bounds(const heat_ctx *c, int want, int64_t **out) {
+  const int64_t N = c->geo.N;
+  int S;
+  int64_t *b;
+  if (c->segments < 0 && c->geo.np <= want) {
+    S = c->geo.np;
+    b = (int64_t *)malloc(sizeof(int64_t) * (size_t)(S + 1));
+    if (!b) return -1;
+    for (int i = 0; i <= S; ++i) b[i] = (int64_t)i * c->geo.nx;
+  } else {
+    if (c->segments > 0 && c->segments < want) want = c->segments;
+    int64_t chunk = (N + want - 1) / want;
+    chunk = (chunk + 63) / 64 * 64;
+    S = (int)((N + chunk - 1) / chunk);
+    b = (int64_t *)malloc(sizeof(int64_t) * (size_t)(S + 1));
+    if (!b) return -1;
+    for (int i = 0; i <= S; ++i) b[i] = (int64_t)i * chunk < N ? (int64_t)i * chunk : N;
+  }
+  *out = b;
+  return S;
+}
+
+int run_persist(heat_ctx *c, int64_t nt) {
+  const int mode = c->dtype == HEAT_F32C ? 2 : (c->arith == HEAT_ARITH_FMA ? 1 : 0);
+  const int resident = mode == 0 ? max_resident<0>(c) : mode == 1 ? max_resident<1>(c) : max_resident<2>(c);
+  if (resident < 1) return HEAT_ECUDA;
+  int64_t *bounds = nullptr;
+  const int S = segment_bounds(c, resident, &bounds);
+  if (S < 1) return HEAT_ENOMEM;
+  int rc = prepare_segments(c, S, bounds);
+  free(bounds);
+  if (rc != HEAT_OK) return rc;
+  PersistArgs a;
+  a.ua = c->buf[c->cur];
+  a.ub = c->buf[c->cur ^ 1];
+  a.N = c->geo.N;
+  a.r = c->r;
+  a.rf = c->rf;
+  a.nt = nt;
+  a.seg = c->seg_start;
+  a.S = S;
+  a.mb = c->mbox;
+  a.st = c->dstat;
+  a.wait_ns = c->wait_ns;
+  a.inj_seg = c->inj_segment;
+  a.inj_step = c->inj_step;
+  const int grid = S < resident ? S : resident;
+  rc = mode == 0 ? launch<0>(c, a, grid) : mode == 1 ? launch<1>(c, a, grid) : launch<2>(c, a, grid);
+  if (rc != HEAT_OK) return rc;
+  c->last_segments = S;
+  if (nt & 1) c->cur ^= 1;
+  c->steps += nt;
+  return HEAT_OK;
+}
+
+}  // namespace heat

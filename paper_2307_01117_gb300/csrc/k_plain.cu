@@ -1,0 +1,123 @@
+// k_plain.cu -- form HEAT_FORM_PLAIN: one step of Eq. 2 (Section 2) over the
+// whole periodic ring per launch.  The ghost exchange between segments is the
+// launch boundary itself (the unsegmented synchronous variant of Section 3.1).
+//
+// Layout: a warp owns 64 consecutive points per iteration; lane l loads points
+// 2l, 2l+1 as one 16-byte vector, neighbours inside the tile come from the
+// adjacent lanes by shuffle, the two tile-edge neighbours are scalar loads
+// (wrapping at 0 and N-1).  The fewer than 64 trailing points are done by
+// scalar threads.  Algorithmic traffic: 8 bytes read + 8 bytes written per
+// point-step for binary64, 4 + 4 for binary32.
+#include "heat_internal.cuh"
+#include "stencil_ops.cuh"
+
+namespace heat {
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kPlainThreads = 256;
+
+template <bool FMA>
+__global__ void __launch_bounds__(kPlainThreads) k_plain_f64(const double *__restrict__ u, double *__restrict__ v,
+                                                             int64_t N, double r) {
+  const int lane = threadIdx.x & 31;
+  const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t warp = gtid >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t ntiles = N >> 6;
+  for (int64_t t = warp; t < ntiles; t += nwarps) {
+    const int64_t b = t << 6;
+    const double2 x = __ldcs(reinterpret_cast<const double2 *>(u + b) + lane);
+    double left = __shfl_up_sync(kFull, x.y, 1);
+    double right = __shfl_down_sync(kFull, x.x, 1);
+    if (lane == 0) left = u[b == 0 ? N - 1 : b - 1];
+    if (lane == 31) right = u[b + 64 == N ? 0 : b + 64];
+    double2 y;
+    y.x = eq2<FMA>(left, x.x, x.y, r);
+    y.y = eq2<FMA>(x.x, x.y, right, r);
+    __stcs(reinterpret_cast<double2 *>(v + b) + lane, y);
+  }
+  const int64_t tail0 = ntiles << 6;
+  if (gtid < N - tail0) {
+    const int64_t g = tail0 + gtid;
+    const double ul = u[g == 0 ? N - 1 : g - 1];
+    const double ur = u[g + 1 == N ? 0 : g + 1];
+    v[g] = eq2<FMA>(ul, u[g], ur, r);
+  }
+}
+
+// Binary32 state, compensated update with a block of one step: the correction
+// starts at zero, so the pair (h, 0) is advanced once and stored as RN(h + l).
+__device__ __forceinline__ float f32c_one_step(float hl, float h, float hr, float rf) {
+  float hn, ln;
+  eq2_f32c(hl, h, hr, 0.0f, 0.0f, 0.0f, rf, hn, ln);
+  return f32c_store(hn, ln);
+}
+
+__global__ void __launch_bounds__(kPlainThreads) k_plain_f32c(const float *__restrict__ u, float *__restrict__ v,
+                                                              int64_t N, float rf) {
+  const int lane = threadIdx.x & 31;
+  const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t warp = gtid >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t ntiles = N >> 7;  // 128 points per warp tile (float4 per lane)
+  for (int64_t t = warp; t < ntiles; t += nwarps) {
+    const int64_t b = t << 7;
+    const float4 x = __ldcs(reinterpret_cast<const float4 *>(u + b) + lane);
+    float left = __shfl_up_sync(kFull, x.w, 1);
+    float right = __shfl_down_sync(kFull, x.x, 1);
+    if (lane == 0) left = u[b == 0 ? N - 1 : b - 1];
+    if (lane == 31) right = u[b + 128 == N ? 0 : b + 128];
+    float4 y;
+    y.x = f32c_one_step(left, x.x, x.y, rf);
+    y.y = f32c_one_step(x.x, x.y, x.z, rf);
+    y.z = f32c_one_step(x.y, x.z, x.w, rf);
+    y.w = f32c_one_step(x.z, x.w, right, rf);
+    __stcs(reinterpret_cast<float4 *>(v + b) + lane, y);
+  }
+  const int64_t tail0 = ntiles << 7;
+  if (gtid < N - tail0) {
+    const int64_t g = tail0 + gtid;
+    const float ul = u[g == 0 ? N - 1 : g - 1];
+    const float ur = u[g + 1 == N ? 0 : g + 1];
+    v[g] = f32c_one_step(ul, u[g], ur, rf);
+  }
+}
+
+// Grid: enough warps to cover the tiles, capped at a whole number of waves
+// (blocks per SM x SMs); at least enough threads for the scalar tail.
+int plain_grid(const heat_ctx *c, int64_t tiles) {
+  const int64_t warps_per_block = kPlainThreads / 32;
+  int64_t blocks = (tiles + warps_per_block - 1) / warps_per_block;
+  const int64_t cap = (int64_t)c->sms * 8;
+  if (blocks > cap) blocks = cap;
+  if (blocks < 1) blocks = 1;
+  return (int)blocks;
+}
+
+}  // namespace
+
+int run_plain(heat_ctx *c, int64_t nt) {
+  const int64_t N = c->geo.N;
+  for (int64_t s = 0; s < nt; ++s) {
+    const void *src = c->buf[c->cur];
+    void *dst = c->buf[c->cur ^ 1];
+    if (c->dtype == HEAT_F64) {
+      const int grid = plain_grid(c, N >> 6);
+      if (c->arith == HEAT_ARITH_FMA)
+        k_plain_f64<true><<<grid, kPlainThreads, 0, c->stream>>>((const double *)src, (double *)dst, N, c->r);
+      else
+        k_plain_f64<false><<<grid, kPlainThreads, 0, c->stream>>>((const double *)src, (double *)dst, N, c->r);
+    } else {
+      const int grid = plain_grid(c, N >> 7);
+      k_plain_f32c<<<grid, kPlainThreads, 0, c->stream>>>((const float *)src, (float *)dst, N, c->rf);
+    }
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return HEAT_ECUDA;
+    c->cur ^= 1;
+    c->steps += 1;
+  }
+  return HEAT_OK;
+}
+
+}  // namespace heat

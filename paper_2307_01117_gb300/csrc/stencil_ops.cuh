@@ -1,0 +1,60 @@
+// stencil_ops.cuh -- the per-point update of Eq. 2 (Section 2) in the
+// library's arithmetic forms.  Every operation is an explicit round-to-nearest
+// intrinsic, so the compiler cannot contract or reorder it.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace heat {
+
+// Eq. 2, exact reading: v = u + r*((ul - 2u) + ur), each operation rounded once.
+// ul - 2u is issued as one fused multiply-add: 2u is exact in binary64 (for
+// |u| <= DBL_MAX/2), so fma(-2, u, ul) rounds the same value ul - 2u once.
+__device__ __forceinline__ double eq2_exact(double ul, double u, double ur, double r) {
+  const double t1 = __fma_rn(-2.0, u, ul);
+  const double t2 = __dadd_rn(t1, ur);
+  const double t3 = __dmul_rn(r, t2);
+  return __dadd_rn(u, t3);
+}
+
+// Eq. 2, fused reading: v = fma(r, (ul - 2u) + ur, u).
+__device__ __forceinline__ double eq2_fma(double ul, double u, double ur, double r) {
+  const double t1 = __fma_rn(-2.0, u, ul);
+  const double t2 = __dadd_rn(t1, ur);
+  return __fma_rn(r, t2, u);
+}
+
+template <bool FMA>
+__device__ __forceinline__ double eq2(double ul, double u, double ur, double r) {
+  return FMA ? eq2_fma(ul, u, ur, r) : eq2_exact(ul, u, ur, r);
+}
+
+// Knuth's TwoSum: s = RN(a + b) and e with s + e == a + b exactly
+// (no ordering assumption on |a|, |b|).
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// One compensated binary32 step on a (hi, lo) pair:
+//   d = ((hl - 2h) + hr) + ((ll - 2l) + lr);  inc = rf*d;
+//   (s, e) = TwoSum(h, inc);  h' = s;  l' = l + e.
+// 2h and 2l are exact in binary32 (below overflow), so the differences are
+// issued as fused multiply-adds with one rounding each.
+__device__ __forceinline__ void eq2_f32c(float hl, float h, float hr, float ll, float l, float lr, float rf,
+                                         float &h_out, float &l_out) {
+  const float dh = __fadd_rn(__fmaf_rn(-2.0f, h, hl), hr);
+  const float dl = __fadd_rn(__fmaf_rn(-2.0f, l, ll), lr);
+  const float d = __fadd_rn(dh, dl);
+  const float inc = __fmul_rn(rf, d);
+  float s, e;
+  two_sum(h, inc, s, e);
+  h_out = s;
+  l_out = __fadd_rn(l, e);
+}
+
+// End of a temporal block: the stored binary32 value RN(h + l).
+__device__ __forceinline__ float f32c_store(float h, float l) { return __fadd_rn(h, l); }
+
+}  // namespace heat

@@ -1,0 +1,251 @@
+"""ctypes binding of libheat.so (include/heat.h), argument marshalling only.
+
+Every function keeps the C name and raises ``HeatError`` on a non-zero status.
+Arrays are numpy binary64 on the host, or torch CUDA tensors / raw device
+pointers for the ``*_device`` calls.  There is no CPU fallback: if libheat.so
+is missing or cannot load, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libheat.so")
+
+HEAT_F64, HEAT_F32C = 0, 1
+HEAT_OK, HEAT_EINVAL, HEAT_ENOMEM, HEAT_ECUDA, HEAT_ETIMEOUT, HEAT_ESTATE, HEAT_ENOTSUP = 0, -1, -2, -3, -4, -5, -6
+HEAT_FORM_PLAIN, HEAT_FORM_PERSIST, HEAT_FORM_TBLOCK, HEAT_FORM_AUTO = 0, 1, 2, 3
+HEAT_ARITH_EXACT, HEAT_ARITH_FMA = 0, 1
+
+FORMS = {"plain": HEAT_FORM_PLAIN, "persist": HEAT_FORM_PERSIST, "tblock": HEAT_FORM_TBLOCK, "auto": HEAT_FORM_AUTO}
+DTYPES = {"f64": HEAT_F64, "f32c": HEAT_F32C}
+
+
+class HeatError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {heat_strerror(code)} ({code})")
+
+
+_lock = threading.Lock()
+_lib = None
+
+# C prototypes: name -> (restype, argtypes)
+_vp, _i64, _i32, _int, _d = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int, ctypes.c_double
+_PROTOS = {
+    "heat_create": (_int, [ctypes.POINTER(_vp), _i64, _i32, _d, _d, _d, _int]),
+    "heat_destroy": (None, [_vp]),
+    "heat_set": (_int, [_vp, _vp, _i64]),
+    "heat_get": (_int, [_vp, _vp, _i64]),
+    "heat_set_device": (_int, [_vp, _vp, _i64]),
+    "heat_get_device": (_int, [_vp, _vp, _i64]),
+    "heat_run": (_int, [_vp, _i64]),
+    "heat_sync": (_int, [_vp]),
+    "heat_set_stream": (_int, [_vp, _vp]),
+    "heat_set_form": (_int, [_vp, _int, _int]),
+    "heat_set_arith": (_int, [_vp, _int]),
+    "heat_set_segments": (_int, [_vp, _int]),
+    "heat_sum": (_int, [_vp, ctypes.POINTER(_d)]),
+    "heat_steps": (_int, [_vp, ctypes.POINTER(_i64)]),
+    "heat_info": (_int, [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i32), ctypes.POINTER(_d), ctypes.POINTER(_int)]),
+    "heat_state_ptr": (_int, [_vp, ctypes.POINTER(_vp)]),
+    "heat_set_wait_limit": (_int, [_vp, _i64]),
+    "heat_inject_stall": (_int, [_vp, _i32, _i64]),
+    "heat_strerror": (ctypes.c_char_p, [_int]),
+}
+
+
+def lib() -> ctypes.CDLL:
+    """Load libheat.so (raises if it was not built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_2307_01117_gb300.build.build()")
+            l = ctypes.CDLL(LIB_PATH)
+            for name, (res, args) in _PROTOS.items():
+                fn = getattr(l, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = l
+        return _lib
+
+
+def _check(code: int, where: str) -> None:
+    if code != HEAT_OK:
+        raise HeatError(code, where)
+
+
+def _dev_ptr(x) -> int:
+    """Device address of a torch CUDA tensor, or an int address."""
+    if isinstance(x, int):
+        return x
+    ptr = getattr(x, "data_ptr", None)
+    if ptr is None:
+        raise TypeError("expected a torch CUDA tensor or an int device address")
+    if not x.is_cuda or not x.is_contiguous():
+        raise ValueError("device tensor must be a contiguous CUDA tensor")
+    return int(ptr())
+
+
+def heat_strerror(code: int) -> str:
+    return lib().heat_strerror(int(code)).decode()
+
+
+def heat_create(nx: int, np_: int, k: float, dt: float, dx: float, dtype: int = HEAT_F64) -> int:
+    h = _vp()
+    _check(lib().heat_create(ctypes.byref(h), int(nx), int(np_), float(k), float(dt), float(dx), int(dtype)),
+           "heat_create")
+    return h.value
+
+
+def heat_destroy(ctx: int) -> None:
+    lib().heat_destroy(ctx)
+
+
+def heat_set(ctx: int, u) -> None:
+    a = np.ascontiguousarray(np.asarray(u, dtype=np.float64))
+    _check(lib().heat_set(ctx, a.ctypes.data, a.size), "heat_set")
+
+
+def heat_get(ctx: int, out: np.ndarray | None = None) -> np.ndarray:
+    if out is None:
+        nx, np_, _, _ = heat_info(ctx)
+        out = np.empty(nx * np_, dtype=np.float64)
+    if out.dtype != np.float64 or not out.flags.c_contiguous:
+        raise ValueError("out must be a contiguous float64 array")
+    _check(lib().heat_get(ctx, out.ctypes.data, out.size), "heat_get")
+    return out
+
+
+def heat_set_device(ctx: int, dev_u, n: int | None = None) -> None:
+    n = int(dev_u.numel()) if n is None else int(n)
+    _check(lib().heat_set_device(ctx, _dev_ptr(dev_u), n), "heat_set_device")
+
+
+def heat_get_device(ctx: int, dev_u, n: int | None = None) -> None:
+    n = int(dev_u.numel()) if n is None else int(n)
+    _check(lib().heat_get_device(ctx, _dev_ptr(dev_u), n), "heat_get_device")
+
+
+def heat_run(ctx: int, nt: int) -> None:
+    _check(lib().heat_run(ctx, int(nt)), "heat_run")
+
+
+def heat_sync(ctx: int) -> None:
+    _check(lib().heat_sync(ctx), "heat_sync")
+
+
+def heat_set_stream(ctx: int, stream) -> None:
+    """stream: a torch.cuda.Stream, a raw cudaStream_t int, or None."""
+    handle = None if stream is None else int(getattr(stream, "cuda_stream", stream))
+    _check(lib().heat_set_stream(ctx, handle), "heat_set_stream")
+
+
+def heat_set_form(ctx: int, form, T: int = 0) -> None:
+    f = FORMS[form] if isinstance(form, str) else int(form)
+    _check(lib().heat_set_form(ctx, f, int(T)), "heat_set_form")
+
+
+def heat_set_segments(ctx: int, segments: int) -> None:
+    _check(lib().heat_set_segments(ctx, int(segments)), "heat_set_segments")
+
+
+def heat_set_arith(ctx: int, arith: int) -> None:
+    _check(lib().heat_set_arith(ctx, int(arith)), "heat_set_arith")
+
+
+def heat_sum(ctx: int) -> float:
+    out = _d()
+    _check(lib().heat_sum(ctx, ctypes.byref(out)), "heat_sum")
+    return out.value
+
+
+def heat_steps(ctx: int) -> int:
+    out = _i64()
+    _check(lib().heat_steps(ctx, ctypes.byref(out)), "heat_steps")
+    return out.value
+
+
+def heat_info(ctx: int) -> tuple[int, int, float, int]:
+    nx, np_, r, dt = _i64(), _i32(), _d(), _int()
+    _check(lib().heat_info(ctx, ctypes.byref(nx), ctypes.byref(np_), ctypes.byref(r), ctypes.byref(dt)), "heat_info")
+    return nx.value, np_.value, r.value, dt.value
+
+
+def heat_state_ptr(ctx: int) -> int:
+    out = _vp()
+    _check(lib().heat_state_ptr(ctx, ctypes.byref(out)), "heat_state_ptr")
+    return out.value
+
+
+def heat_set_wait_limit(ctx: int, ns: int) -> None:
+    _check(lib().heat_set_wait_limit(ctx, int(ns)), "heat_set_wait_limit")
+
+
+def heat_inject_stall(ctx: int, segment: int, from_step: int = 0) -> None:
+    _check(lib().heat_inject_stall(ctx, int(segment), int(from_step)), "heat_inject_stall")
+
+
+class Heat:
+    """Owning wrapper: a ring of np_ x nx points advanced by Eq. 2 on the GPU."""
+
+    def __init__(self, nx: int, np_: int, k: float, dt: float, dx: float, dtype="f64", form="auto", T: int = 0,
+                 arith: int = HEAT_ARITH_EXACT, stream=None):
+        self.ctx = heat_create(nx, np_, k, dt, dx, DTYPES[dtype] if isinstance(dtype, str) else int(dtype))
+        try:
+            heat_set_form(self.ctx, form, T)
+            heat_set_arith(self.ctx, arith)
+            if stream is not None:
+                heat_set_stream(self.ctx, stream)
+        except Exception:
+            self.close()
+            raise
+        self.nx, self.np_ = int(nx), int(np_)
+        self.n = self.nx * self.np_
+
+    def set(self, u) -> "Heat":
+        heat_set(self.ctx, u)
+        return self
+
+    def get(self) -> np.ndarray:
+        return heat_get(self.ctx)
+
+    def run(self, nt: int) -> "Heat":
+        heat_run(self.ctx, nt)
+        return self
+
+    def sync(self) -> None:
+        heat_sync(self.ctx)
+
+    def sum(self) -> float:
+        return heat_sum(self.ctx)
+
+    @property
+    def r(self) -> float:
+        return heat_info(self.ctx)[2]
+
+    @property
+    def steps(self) -> int:
+        return heat_steps(self.ctx)
+
+    def close(self) -> None:
+        if getattr(self, "ctx", None):
+            heat_destroy(self.ctx)
+            self.ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

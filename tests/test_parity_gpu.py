@@ -1,0 +1,170 @@
+"""GPU parity: every kernel form against the CPU oracle, element by element,
+through the C ABI (binding in paper_2307_01117_gb300.heat).
+
+Bar: bitwise equality for binary64 with the exact reading of Eq. 2 and for the
+fused reading against the oracle's fused reading; the fused reading is also
+within 1e-12 * max|u0| of the exact one; binary32-compensated state bitwise
+against the oracle's compensated form with the same block length.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2307_01117_gb300 import heat as H
+from paper_2307_01117_gb300 import workloads
+
+pytestmark = pytest.mark.gpu
+
+FORMS_F64 = [("plain", 0), ("persist", 0)]
+FORMS_F32C = [("plain", 0), ("persist", 0)]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2307_01117_gb300 import build
+    build.build()
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+
+
+def run_gpu(u0, np_, r, nt, form="plain", T=0, dtype="f64", arith=H.HEAT_ARITH_EXACT, chunks=None):
+    n = len(u0)
+    assert n % np_ == 0
+    with H.Heat(n // np_, np_, r, 1.0, 1.0, dtype=dtype, form=form, T=T, arith=arith) as h:
+        h.set(u0)
+        for c in (chunks or [nt]):
+            h.run(c)
+        out = h.get()
+        assert h.steps == nt
+    return out
+
+
+def same_bits(a, b):
+    return np.array_equal(np.asarray(a).view(np.uint64), np.asarray(b).view(np.uint64))
+
+
+SIZES = [(1, 1), (2, 1), (3, 1), (5, 1), (7, 1), (64, 1), (65, 1), (127, 1), (128, 1), (129, 1),
+         (1000, 4), (4000, 4), (65537, 1), (3 * (7 * 1024 + 5), 3), (16 * 4099, 16)]
+
+
+@pytest.mark.parametrize("form,T", FORMS_F64)
+@pytest.mark.parametrize("n,np_", SIZES)
+def test_f64_exact_bitwise(form, T, n, np_):
+    u0 = workloads.uniform(n, 1000 + n, -1, 1)
+    for nt, r in [(0, 0.25), (1, 0.5), (2, 0.37), (17, 0.25), (64, 0.5)]:
+        ref = oracle.run(u0, r, nt)
+        got = run_gpu(u0, np_, r, nt, form, T)
+        assert same_bits(got, ref), (n, np_, nt, r, int(np.sum(got != ref)))
+
+
+@pytest.mark.parametrize("form,T", FORMS_F64)
+def test_paper_config_small_ring(form, T):
+    """np=4 x nx=1000, nt=100, k=0.5, dt=dx=1, u[g]=g (Section 2's initial condition)."""
+    u0 = workloads.ramp(4000)
+    r = oracle.coef(0.5, 1.0, 1.0)
+    ref = oracle.run(u0, r, 100)
+    with H.Heat(1000, 4, 0.5, 1.0, 1.0, form=form, T=T) as h:
+        h.set(u0).run(100)
+        got = h.get()
+        assert h.sum() == 7998000.0
+    assert same_bits(got, ref)
+
+
+@pytest.mark.parametrize("form,T", FORMS_F64)
+@pytest.mark.parametrize("n", [5, 64, 4000, 100003])
+def test_f64_fma_form(form, T, n):
+    u0 = workloads.uniform(n, 77, -3, 3)
+    r, nt = 0.4, 50
+    got = run_gpu(u0, 1, r, nt, form, T, arith=H.HEAT_ARITH_FMA)
+    assert same_bits(got, oracle.run(u0, r, nt, fma=True))
+    exact = oracle.run(u0, r, nt)
+    assert np.max(np.abs(got - exact)) <= 1e-12 * np.max(np.abs(u0))
+
+
+@pytest.mark.parametrize("form,T", FORMS_F32C)
+@pytest.mark.parametrize("n", [1, 3, 128, 129, 4000, 100003])
+def test_f32c_bitwise(form, T, n):
+    u0 = workloads.uniform(n, 5 + n, -1, 1)
+    u32 = u0.astype(np.float32)
+    for nt, r in [(1, 0.5), (13, 0.3), (40, 0.25)]:
+        Tb = T if form == "tblock" else 1
+        ref = oracle.run_f32c(u32, np.float32(r), nt, max(Tb, 1)).astype(np.float64)
+        got = run_gpu(u0, 1, r, nt, form, T, dtype="f32c")
+        assert np.array_equal(got, ref), (n, nt, r)
+
+
+def test_restart_invariance():
+    u0 = workloads.uniform(10007, 3, -1, 1)
+    a = run_gpu(u0, 1, 0.3, 30, chunks=[7, 0, 13, 10])
+    b = run_gpu(u0, 1, 0.3, 30)
+    assert same_bits(a, b)
+
+
+def test_sum_is_conserved_and_close_to_exact():
+    n = 1 << 20
+    u0 = workloads.uniform(n, 9, -1, 1)
+    with H.Heat(n // 4, 4, 0.25, 1.0, 1.0) as h:
+        h.set(u0)
+        s0 = h.sum()
+        assert abs(s0 - math.fsum(u0)) <= n * 1.2e-16 * np.sum(np.abs(u0))
+        h.run(100)
+        s1 = h.sum()
+        u = h.get()
+    assert abs(s1 - math.fsum(u)) <= n * 1.2e-16 * np.sum(np.abs(u))
+    assert abs(s1 - s0) <= 4 * 100 * n * 2.2e-16
+
+
+def test_sum_is_deterministic():
+    n = 3 * 10**6 + 7
+    u0 = workloads.uniform(n, 10, -1, 1)
+    with H.Heat(n, 1, 0.25, 1.0, 1.0) as h:
+        h.set(u0)
+        vals = {h.sum() for _ in range(5)}
+    assert len(vals) == 1
+
+
+def test_device_transfers_match_host():
+    import torch
+    n = 12345
+    u0 = workloads.uniform(n, 4, -1, 1)
+    t = torch.from_numpy(u0).cuda()
+    out = torch.empty_like(t)
+    for dtype in ("f64", "f32c"):
+        with H.Heat(n, 1, 0.25, 1.0, 1.0, dtype=dtype) as h:
+            H.heat_set_device(h.ctx, t)
+            h.run(5)
+            H.heat_get_device(h.ctx, out)
+            torch.cuda.synchronize()
+            host = h.get()
+        assert np.array_equal(out.cpu().numpy(), host)
+
+
+def test_torch_stream_ordering():
+    import torch
+    n = 1 << 16
+    u0 = workloads.uniform(n, 6, -1, 1)
+    s = torch.cuda.Stream()
+    with H.Heat(n, 1, 0.3, 1.0, 1.0, stream=s) as h:
+        h.set(u0).run(20)
+        got = h.get()
+    assert same_bits(got, oracle.run(u0, 0.3, 20))
+
+
+def test_argument_errors():
+    with H.Heat(100, 2, 0.25, 1.0, 1.0) as h:
+        with pytest.raises(H.HeatError) as e:
+            H.heat_set(h.ctx, np.zeros(199))
+        assert e.value.code == H.HEAT_EINVAL
+        with pytest.raises(H.HeatError) as e:
+            H.heat_run(h.ctx, -1)
+        assert e.value.code == H.HEAT_EINVAL
+        with pytest.raises(H.HeatError):
+            H.heat_set_form(h.ctx, 9, 0)
+        with pytest.raises(H.HeatError):
+            H.heat_set_form(h.ctx, 2, 65)
+        with pytest.raises(H.HeatError):
+            H.heat_set_arith(h.ctx, 5)
+        H.heat_run(h.ctx, 0)
+        assert h.steps == 0

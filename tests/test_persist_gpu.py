@@ -1,0 +1,86 @@
+"""Persistent flag-queue form: segmentation choices, and the bounded waits.
+
+The fault is made on the host side: a test hook tells one segment's CTA to stop
+publishing its edge values, so its neighbours' bounded waits run out, the run
+reports HEAT_ETIMEOUT at the next sync, and every kernel returns normally.  No
+GPU fault, trap or unbounded spin is involved.
+"""
+import time
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2307_01117_gb300 import heat as H
+from paper_2307_01117_gb300 import workloads
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2307_01117_gb300 import build
+    build.build()
+
+
+def bits(a):
+    return np.asarray(a).view(np.uint64)
+
+
+@pytest.mark.parametrize("segments", [0, -1, 1, 2, 3, 7, 64])
+@pytest.mark.parametrize("nx,np_", [(1000, 4), (4099, 16), (65, 3), (1, 5), (1 << 14, 256)])
+def test_segmentations_agree_bitwise(segments, nx, np_):
+    n = nx * np_
+    u0 = workloads.uniform(n, 50 + segments, -1, 1)
+    ref = oracle.run(u0, 0.3, 37)
+    with H.Heat(nx, np_, 0.3, 1.0, 1.0, form="persist") as h:
+        H.heat_set_segments(h.ctx, segments)
+        h.set(u0).run(37)
+        got = h.get()
+    assert np.array_equal(bits(got), bits(ref))
+
+
+def test_paper_partitions_one_cta_each():
+    """np=256 partitions, one segment (CTA) per partition as in Section 2."""
+    nx, np_ = 2048, 256
+    u0 = workloads.uniform_plus_mode(nx * np_, seed=0, m=3)
+    ref = oracle.run_segmented(u0, np_, 0.25, 20)
+    with H.Heat(nx, np_, 0.25, 1.0, 1.0, form="persist") as h:
+        H.heat_set_segments(h.ctx, -1)
+        h.set(u0).run(20)
+        got = h.get()
+    assert np.array_equal(bits(got), bits(ref))
+
+
+@pytest.mark.parametrize("seg,step", [(0, 0), (3, 5), (6, 17)])
+def test_stalled_producer_times_out_cleanly(seg, step):
+    n = 7 * 4096
+    u0 = workloads.uniform(n, 3, -1, 1)
+    with H.Heat(4096, 7, 0.25, 1.0, 1.0, form="persist") as h:
+        H.heat_set_segments(h.ctx, 7)
+        H.heat_set_wait_limit(h.ctx, 50_000_000)       # 50 ms
+        H.heat_inject_stall(h.ctx, seg, step)
+        h.set(u0)
+        t0 = time.time()
+        h.run(40)                                     # launch succeeds
+        with pytest.raises(H.HeatError) as e:
+            h.sync()
+        assert e.value.code == H.HEAT_ETIMEOUT
+        assert time.time() - t0 < 10.0
+        # the context refuses further runs until the state is reloaded ...
+        with pytest.raises(H.HeatError) as e:
+            h.run(1)
+        assert e.value.code == H.HEAT_ESTATE
+        with pytest.raises(H.HeatError):
+            h.get()
+        # ... and is fully usable again after heat_set with the hook cleared
+        H.heat_inject_stall(h.ctx, -1, 0)
+        h.set(u0).run(40)
+        got = h.get()
+    assert np.array_equal(bits(got), bits(oracle.run(u0, 0.25, 40)))
+
+
+def test_device_stays_usable_after_timeout():
+    import torch
+    x = torch.arange(10, device="cuda", dtype=torch.float64)
+    assert float(x.sum().item()) == 45.0
