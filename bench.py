@@ -282,36 +282,41 @@ def main() -> int:
     value = world * point_steps * args.steps / (ms_max * 1e-3) / 1e9
 
     # which kernel dominates and how long one launch takes (CUDA events on the ctx stream)
-    form_used = H.heat_form_used(ctx) if hasattr(H, "heat_form_used") else args.form
-    launches_per_run = nt if form_used in ("plain", "auto") else 1
-    if form_used == "tblock":
-        T = args.T or 8
-        launches_per_run = -(-nt // T)
+    last = H.heat_last_run(ctx)
+    form_used = last["form"]
+    launches_per_run = max(1, last["launches"])
     kernel_ms = statistics.mean(run_ms) / launches_per_run
     pk = peaks()
     steps_per_launch = nt / launches_per_run
-    units = float(n) * steps_per_launch
+    units = float(n) * steps_per_launch          # point-steps per launch
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    kname = {("plain", "f64"): "k_plain_f64", ("plain", "f32c"): "k_plain_f32c", ("persist", "f64"): "k_persist",
+             ("persist", "f32c"): "k_persist", ("tblock", "f64"): "k_tblock", ("tblock", "f32c"): "k_tblock"}[
+        (form_used, w["dtype"])]
+    srcs = {"k_plain_f64": ["k_plain.cu"], "k_plain_f32c": ["k_plain.cu"], "k_persist": ["k_persist.cu"],
+            "k_tblock": ["k_tblock.cu"]}[kname]
+    srcs = [f"paper_2307_01117_gb300/csrc/{x}" for x in srcs] + ["paper_2307_01117_gb300/csrc/stencil_ops.cuh"]
+    # algorithmic HBM bytes: each point read once and written once per launch, whatever the steps per launch
+    # (one-step forms: 16 B per point-step in binary64; forms that keep T steps on chip: 16/T)
+    elem = 8.0 if w["dtype"] == "f64" else 4.0
+    alg_bytes = 2.0 * elem * float(n) * (steps_per_launch if form_used == "persist" else 1.0)
+    hbm_achieved = alg_bytes / (kernel_ms * 1e-3) / 1e9
+    roof_hbm = {"bound": "hbm", "achieved": hbm_achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                "frac": hbm_achieved / pk["hbm_gbs"], "peak_src": pk["src"], "alg_bytes_per_launch": alg_bytes}
     if w["dtype"] == "f64":
         dp_ops = DP_OPS[arith] * units
         # DP pipe: 2 lane-operations per clock per SM (GB300 nominal 1.25 TFLOP/s FP64 with FMA = 2 flops)
-        sms = torch.cuda.get_device_properties(local).multi_processor_count
         dp_peak = 2.0 * sms * pk["sm_max_mhz"] * 1e6 / 1e9
         achieved = dp_ops / (kernel_ms * 1e-3) / 1e9
         roofline = {"bound": "alu", "achieved": achieved, "peak": dp_peak, "unit": "G DP-op/s",
-                    "frac": achieved / dp_peak, "peak_src": f"2 DP ops/clk/SM x {sms} SMs x {pk['sm_max_mhz']:.0f} MHz"}
+                    "frac": achieved / dp_peak,
+                    "peak_src": f"2 DP ops/clk/SM x {sms} SMs x {pk['sm_max_mhz']:.0f} MHz (max SM clock)",
+                    "alg_ops_per_launch": dp_ops}
     else:
-        achieved = None
-        roofline = {}
-    alg_bytes = (16.0 if w["dtype"] == "f64" else 8.0) * float(n) * (1 if form_used != "tblock" else 1)
-    hbm_achieved = alg_bytes * launches_per_run / (statistics.mean(run_ms) * 1e-3) / 1e9
-    roof_hbm = {"bound": "hbm", "achieved": hbm_achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                "frac": hbm_achieved / pk["hbm_gbs"], "peak_src": pk["src"]}
-    if w["dtype"] != "f64":
-        roofline = roof_hbm
-    kname = {"plain": "k_plain_f64" if w["dtype"] == "f64" else "k_plain_f32c"}.get(form_used, "k_plain_f64")
-    srcs = ["paper_2307_01117_gb300/csrc/k_plain.cu", "paper_2307_01117_gb300/csrc/stencil_ops.cuh"]
+        roofline = dict(roof_hbm)
     roofline["traffic"] = profile_traffic(kname, args.workload, srcs)
     roofline["kernel"] = kname
+    roofline["launch_ms"] = kernel_ms
 
     # end to end through the C ABI with host buffers: H2D of u0, run, sum, D2H of the state
     e2e = None
@@ -350,7 +355,8 @@ def main() -> int:
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64" if w["dtype"] == "f64" else "f32", "data": "synthetic",
             "config": {"workload": args.workload, "nx": w["nx"], "np": w["np"], "N": n, "nt": nt, "k": w["k"],
-                       "dt": w["dt"], "dx": w["dx"], "init": w["init"], "form": form_used, "T": args.T,
+                       "dt": w["dt"], "dx": w["dx"], "init": w["init"], "form": form_used, "T": last["T"],
+                       "segments": last["segments"] if form_used != "plain" else None,
                        "arith": args.arith, "l2": "inputs larger than L2 (no flush needed)" if n * 8 > 2 * 135e6
                        else "L2-resident ring", "parallelism": "replicas" if world > 1 else "single GPU"},
             "roofline": roofline, "roofline_hbm": roof_hbm, "cpu_baseline": cb, "e2e": e2e,

@@ -152,6 +152,12 @@ int heat_sum(heat_ctx *c, double *out);
  * heat_get + this count is a checkpoint; heat_set restores). */
 int heat_steps(const heat_ctx *c, int64_t *out);
 
+/* What the last heat_run did: the form it used (HEAT_FORM_AUTO resolved), the
+ * temporal block depth (1 for the one-step forms), the number of stencil kernel
+ * launches it queued, and the persistent forms' segment count.  Any pointer may
+ * be NULL. */
+int heat_last_run(const heat_ctx *c, int *form, int *T, int64_t *launches, int *segments);
+
 /* Ring geometry and the coefficient actually used. */
 int heat_info(const heat_ctx *c, int64_t *nx, int32_t *np, double *r, int *dtype);
 

@@ -196,12 +196,24 @@ int heat_run(heat_ctx *c, int64_t nt) {
   if (nt == 0) return HEAT_OK;
   int form = c->form;
   if (form == HEAT_FORM_AUTO) form = HEAT_FORM_PLAIN;
+  c->last_form = form;
+  c->last_T = 1;
+  c->last_launches = 0;
   switch (form) {
     case HEAT_FORM_PLAIN: return heat::run_plain(c, nt);
     case HEAT_FORM_PERSIST: return heat::run_persist(c, nt);
     case HEAT_FORM_TBLOCK: return heat::run_tblock(c, nt);
     default: return HEAT_EINVAL;
   }
+}
+
+int heat_last_run(const heat_ctx *c, int *form, int *T, int64_t *launches, int *segments) {
+  if (!c) return HEAT_EINVAL;
+  if (form) *form = c->last_form;
+  if (T) *T = c->last_T;
+  if (launches) *launches = c->last_launches;
+  if (segments) *segments = c->last_segments;
+  return HEAT_OK;
 }
 
 int heat_sync(heat_ctx *c) {

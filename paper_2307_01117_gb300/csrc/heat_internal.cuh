@@ -66,6 +66,9 @@ struct heat_ctx {
   int mbox_segments;             // capacity of mbox / seg_start
   int segments;                  // persistent segmentation: 0 auto, -1 one per partition, >0 count
   int last_segments;             // segments used by the last persistent run
+  int last_form;                 // form used by the last heat_run
+  int last_T;                    // temporal block depth used by the last heat_run
+  int64_t last_launches;         // stencil kernel launches queued by the last heat_run
   double *partials;              // reduction scratch, device
   double *hsum;                  // pinned host word for heat_sum
   int64_t wait_ns;

@@ -299,6 +299,7 @@ int run_persist(heat_ctx *c, int64_t nt) {
   rc = mode == 0 ? launch<0>(c, a, grid) : mode == 1 ? launch<1>(c, a, grid) : launch<2>(c, a, grid);
   if (rc != HEAT_OK) return rc;
   c->last_segments = S;
+  c->last_launches = 1;
   if (nt & 1) c->cur ^= 1;
   c->steps += nt;
   return HEAT_OK;

@@ -116,6 +116,7 @@ int run_plain(heat_ctx *c, int64_t nt) {
     if (e != cudaSuccess) return HEAT_ECUDA;
     c->cur ^= 1;
     c->steps += 1;
+    c->last_launches += 1;
   }
   return HEAT_OK;
 }

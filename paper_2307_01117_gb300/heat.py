@@ -51,6 +51,8 @@ _PROTOS = {
     "heat_set_segments": (_int, [_vp, _int]),
     "heat_sum": (_int, [_vp, ctypes.POINTER(_d)]),
     "heat_steps": (_int, [_vp, ctypes.POINTER(_i64)]),
+    "heat_last_run": (_int, [_vp, ctypes.POINTER(_int), ctypes.POINTER(_int), ctypes.POINTER(_i64),
+                             ctypes.POINTER(_int)]),
     "heat_info": (_int, [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i32), ctypes.POINTER(_d), ctypes.POINTER(_int)]),
     "heat_state_ptr": (_int, [_vp, ctypes.POINTER(_vp)]),
     "heat_set_wait_limit": (_int, [_vp, _i64]),
@@ -169,6 +171,15 @@ def heat_steps(ctx: int) -> int:
     out = _i64()
     _check(lib().heat_steps(ctx, ctypes.byref(out)), "heat_steps")
     return out.value
+
+
+def heat_last_run(ctx: int) -> dict:
+    """Form, block depth T, stencil launches and segments of the last heat_run."""
+    f, T, n, sg = _int(), _int(), _i64(), _int()
+    _check(lib().heat_last_run(ctx, ctypes.byref(f), ctypes.byref(T), ctypes.byref(n), ctypes.byref(sg)),
+           "heat_last_run")
+    names = {v: k for k, v in FORMS.items()}
+    return {"form": names.get(f.value, str(f.value)), "T": T.value, "launches": n.value, "segments": sg.value}
 
 
 def heat_info(ctx: int) -> tuple[int, int, float, int]:
