@@ -177,6 +177,28 @@ int heat_set_wait_limit(heat_ctx *c, int64_t ns);
  * disables the hook.  No GPU fault or trap is involved. */
 int heat_inject_stall(heat_ctx *c, int32_t segment, int64_t from_step);
 
+/* Allocation-free stepper for callers that cannot allocate device memory
+ * (inside CUDA graph capture, in real-time loops that must stay off the
+ * allocator, or under another framework's memory pool).  The paper has no
+ * counterpart: this is a packaging of the plain form.
+ *   dev_u0  device input, n binary64 values in ring order, only read;
+ *   dev_u   device output, n binary64 values, receives u^nt;
+ *           both 16-byte aligned and not overlapping;
+ *   n       1 .. 1048576 points (larger rings -> HEAT_EINVAL: the library's one
+ *           fixed scratch array holds 2^20 values);
+ *   k, dt, dx, arith   as for heat_create / heat_set_arith;
+ *   cuda_stream        cudaStream_t the steps are queued on (NULL = default).
+ * Queues nt launches and returns without waiting.  It calls no cudaMalloc,
+ * cudaFree or other allocating routine: the buffer a multi-step run needs
+ * besides input and output is a fixed 8 MiB device array that every GPU loading
+ * this library holds until the process exits.  The first call on each device
+ * looks up that array's device address (cudaGetSymbolAddress) with the device
+ * current; make that first call before any stream capture.  All calls on a
+ * device share the array, so calls whose work overlaps on the GPU (two streams,
+ * two host threads) race and must be ordered by the caller. */
+int heat_run_noalloc(const double *dev_u0, double *dev_u, int64_t n, double k, double dt, double dx,
+                     int64_t nt, int arith, void *cuda_stream);
+
 /* Static text for a status code. */
 const char *heat_strerror(int code);
 

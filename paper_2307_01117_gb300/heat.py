@@ -57,6 +57,7 @@ _PROTOS = {
     "heat_state_ptr": (_int, [_vp, ctypes.POINTER(_vp)]),
     "heat_set_wait_limit": (_int, [_vp, _i64]),
     "heat_inject_stall": (_int, [_vp, _i32, _i64]),
+    "heat_run_noalloc": (_int, [_vp, _vp, _i64, _d, _d, _d, _i64, _int, _vp]),
     "heat_strerror": (ctypes.c_char_p, [_int]),
 }
 
@@ -200,6 +201,14 @@ def heat_set_wait_limit(ctx: int, ns: int) -> None:
 
 def heat_inject_stall(ctx: int, segment: int, from_step: int = 0) -> None:
     _check(lib().heat_inject_stall(ctx, int(segment), int(from_step)), "heat_inject_stall")
+
+
+def heat_run_noalloc(dev_u0, dev_u, n: int, k: float, dt: float, dx: float, nt: int,
+                     arith: int = HEAT_ARITH_EXACT, stream=None) -> None:
+    """Allocation-free run: u^nt of dev_u0 into dev_u (device tensors or addresses)."""
+    handle = None if stream is None else int(getattr(stream, "cuda_stream", stream))
+    _check(lib().heat_run_noalloc(_dev_ptr(dev_u0), _dev_ptr(dev_u), int(n), float(k), float(dt), float(dx),
+                                  int(nt), int(arith), handle), "heat_run_noalloc")
 
 
 class Heat:
