@@ -1,5 +1,297 @@
-// k_tblock.cu -- form HEAT_FORM_TBLOCK (placeholder until the temporal-blocking kernel lands).
+// k_tblock.cu -- form HEAT_FORM_TBLOCK: temporal blocking.  Each launch
+// advances the ring by T steps of Eq. 2 (Section 2); the last launch of a run
+// may advance fewer.  Ghost exchange between tiles is implicit: every tile reads
+// a T-wide halo on each side at the launch's start time and recomputes it.
+//
+// Per warp: a window of WIN = 32*E consecutive points, W = WIN - 2T of which are
+// its output.  The window is staged from HBM into shared memory by one 1D bulk
+// TMA copy (cp.async.bulk, completion on an mbarrier), double-buffered so the
+// next tile's copy is in flight while this one is computed.  Lane l then holds
+// window points 32k + l (k = 0..E-1) in registers; one step needs, per point,
+// the left and right neighbours, which come from lanes l-1 and l+1 by shuffle
+// (lane 0 takes lane 31's value of register k-1, lane 31 takes lane 0's value of
+// register k+1).  After s steps the points s .. WIN-1-s of the window are exact;
+// after T steps the middle W points are stored.  Tiles whose window wraps
+// around the ring's ends are loaded with plain indexed loads instead of TMA.
+//
+// Binary32 compensated state: registers carry (h, l) pairs; the block's T steps
+// are one compensation block, stored as RN(h + l) (the library's HEAT_F32C
+// definition).
+//
+// Algorithmic HBM traffic per launch: N points read + N written (16 B per point
+// per T steps in binary64, 8 B in binary32); the halo re-read adds WIN/W.
 #include "heat_internal.cuh"
+#include "stencil_ops.cuh"
+
 namespace heat {
-int run_tblock(heat_ctx *, int64_t) { return HEAT_ENOTSUP; }
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kWarps = 4;  // warps per CTA
+constexpr long long kMaxWaitSpins = 1LL << 24;
+
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long *bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+__device__ __forceinline__ void bulk_load(void *sdst, const void *gsrc, unsigned bytes, unsigned long long *bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(sdst)),
+               "l"(gsrc), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// ---- per-dtype register state and update --------------------------------------------
+template <int MODE>
+struct TB;
+
+template <int MODE>
+struct TBf64 {
+  using T = double;
+  static constexpr int E = 16;  // points per lane: window of 512
+  static constexpr int kAlign = 2;  // elements per 16 bytes
+  struct Reg {
+    double x[E];
+  };
+  static __device__ __forceinline__ void load(Reg &R, int k, double v) { R.x[k] = v; }
+  static __device__ __forceinline__ double store(const Reg &R, int k) { return R.x[k]; }
+  static __device__ __forceinline__ void step(Reg &R, int lane, double r, float) {
+    const int lm = (lane + 31) & 31, lp = (lane + 1) & 31;
+    double Lprev = __shfl_sync(kFull, R.x[0], lm);
+    double Rcur = __shfl_sync(kFull, R.x[0], lp);
+#pragma unroll
+    for (int k = 0; k < E; ++k) {
+      const double Lk = k == 0 ? Lprev : __shfl_sync(kFull, R.x[k], lm);
+      const double Rn = k + 1 < E ? __shfl_sync(kFull, R.x[k + 1], lp) : Rcur;
+      const double left = lane == 0 ? Lprev : Lk;
+      const double right = lane == 31 ? Rn : Rcur;
+      R.x[k] = eq2<MODE == 1>(left, R.x[k], right, r);
+      Lprev = Lk;
+      Rcur = Rn;
+    }
+  }
+};
+template <>
+struct TB<0> : TBf64<0> {};
+template <>
+struct TB<1> : TBf64<1> {};
+
+template <>
+struct TB<2> {
+  using T = float;
+  static constexpr int E = 32;  // window of 1024
+  static constexpr int kAlign = 4;
+  struct Reg {
+    float h[E];
+    float l[E];
+  };
+  static __device__ __forceinline__ void load(Reg &R, int k, float v) {
+    R.h[k] = v;
+    R.l[k] = 0.0f;
+  }
+  static __device__ __forceinline__ float store(const Reg &R, int k) { return f32c_store(R.h[k], R.l[k]); }
+  static __device__ __forceinline__ void step(Reg &R, int lane, double, float rf) {
+    const int lm = (lane + 31) & 31, lp = (lane + 1) & 31;
+    float Lh = __shfl_sync(kFull, R.h[0], lm), Ll = __shfl_sync(kFull, R.l[0], lm);
+    float Rh = __shfl_sync(kFull, R.h[0], lp), Rl = __shfl_sync(kFull, R.l[0], lp);
+#pragma unroll
+    for (int k = 0; k < E; ++k) {
+      const float Lkh = k == 0 ? Lh : __shfl_sync(kFull, R.h[k], lm);
+      const float Lkl = k == 0 ? Ll : __shfl_sync(kFull, R.l[k], lm);
+      const float Rnh = k + 1 < E ? __shfl_sync(kFull, R.h[k + 1], lp) : Rh;
+      const float Rnl = k + 1 < E ? __shfl_sync(kFull, R.l[k + 1], lp) : Rl;
+      const float lh = lane == 0 ? Lh : Lkh, ll = lane == 0 ? Ll : Lkl;
+      const float rh = lane == 31 ? Rnh : Rh, rl = lane == 31 ? Rnl : Rl;
+      float hn, ln;
+      eq2_f32c(lh, R.h[k], rh, ll, R.l[k], rl, rf, hn, ln);
+      R.h[k] = hn;
+      R.l[k] = ln;
+      Lh = Lkh;
+      Ll = Lkl;
+      Rh = Rnh;
+      Rl = Rnl;
+    }
+  }
+};
+
+struct TBArgs {
+  const void *src;
+  void *dst;
+  int64_t N;
+  double r;
+  float rf;
+  int T;        // halo width (the block depth)
+  int steps;    // steps this launch (<= T)
+  int64_t ntiles;
+  DevStatus *st;
+};
+
+template <int MODE>
+__global__ void __launch_bounds__(kWarps * 32) k_tblock(TBArgs a) {
+  using P = TB<MODE>;
+  using T = typename P::T;
+  constexpr int E = P::E;
+  constexpr int WIN = 32 * E;
+  constexpr int BUF = WIN + P::kAlign;  // elements per staging buffer
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  const int lane = threadIdx.x & 31;
+  const int wib = threadIdx.x >> 5;
+  T *buf0 = reinterpret_cast<T *>(smem_raw) + (size_t)wib * 2 * BUF;
+  __shared__ unsigned long long bars[kWarps][2];
+  unsigned long long *bar = bars[wib];
+
+  const T *src = (const T *)a.src;
+  T *dst = (T *)a.dst;
+  const int64_t N = a.N;
+  const int W = WIN - 2 * a.T;
+  const int64_t warp = ((int64_t)blockIdx.x * kWarps + wib);
+  const int64_t nwarps = (int64_t)gridDim.x * kWarps;
+
+  if (lane == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    fence_proxy_async();
+  }
+  __syncwarp();
+
+  // A tile is staged by TMA when its window [ws, ws + WIN) lies inside the ring
+  // (no wrap); the copy starts at ws rounded down to 16 bytes.
+  auto window_start = [&](int64_t tile) -> int64_t { return tile * (int64_t)W - a.T; };
+  auto tma_ok = [&](int64_t ws) -> bool { return ws >= 0 && ws + WIN + P::kAlign <= N; };
+  auto issue = [&](int64_t tile, int b) {
+    const int64_t ws = window_start(tile);
+    if (!tma_ok(ws)) return;
+    const int64_t ws_al = ws & ~(int64_t)(P::kAlign - 1);
+    if (lane == 0) {
+      fence_proxy_async();
+      mbar_expect_tx(&bar[b], (unsigned)(BUF * sizeof(T)));
+      bulk_load(buf0 + b * BUF, src + ws_al, (unsigned)(BUF * sizeof(T)), &bar[b]);
+    }
+  };
+
+  unsigned phase0 = 0u, phase1 = 0u;  // mbarrier phase parity per staging buffer
+  int b = 0;
+  if (warp < a.ntiles) issue(warp, 0);
+  for (int64_t tile = warp; tile < a.ntiles; tile += nwarps) {
+    const int64_t next = tile + nwarps;
+    __syncwarp();
+    if (next < a.ntiles) issue(next, b ^ 1);
+    const int64_t ws = window_start(tile);
+    typename P::Reg R;
+    if (tma_ok(ws)) {
+      // every lane observes the barrier; the loop exits for the whole warp at once
+      bool done = false;
+      for (long long spin = 0; spin < kMaxWaitSpins && !done; ++spin)
+        done = __all_sync(kFull, mbar_try_wait(&bar[b], b ? phase1 : phase0));
+      if (!done) {  // the copy did not complete: record and stop this warp
+        if (lane == 0 && atomicCAS(&a.st->code, HEAT_OK, HEAT_ETIMEOUT) == HEAT_OK) {
+          a.st->segment = -1;
+          a.st->step = tile;
+        }
+        return;
+      }
+      if (b) phase1 ^= 1u; else phase0 ^= 1u;
+      const T *sb = buf0 + b * BUF + (int)(ws - (ws & ~(int64_t)(P::kAlign - 1)));
+#pragma unroll
+      for (int k = 0; k < E; ++k) P::load(R, k, sb[32 * k + lane]);
+    } else {
+#pragma unroll
+      for (int k = 0; k < E; ++k) {
+        int64_t g = (ws + 32 * k + lane) % N;
+        if (g < 0) g += N;
+        P::load(R, k, src[g]);
+      }
+    }
+    for (int s = 0; s < a.steps; ++s) P::step(R, lane, a.r, a.rf);
+    // store the W exact points of the window: indices T .. WIN-1-T
+#pragma unroll
+    for (int k = 0; k < E; ++k) {
+      const int i = 32 * k + lane;
+      const int64_t g = ws + i;
+      if (i >= a.T && i < WIN - a.T && g < N) dst[g] = P::store(R, k);
+    }
+    b ^= 1;
+  }
+}
+
+template <int MODE>
+size_t smem_bytes() {
+  using P = TB<MODE>;
+  return (size_t)kWarps * 2 * (32 * P::E + P::kAlign) * sizeof(typename P::T);
+}
+
+template <int MODE>
+int launch_tb(heat_ctx *c, const void *src, void *dst, int T, int steps) {
+  using P = TB<MODE>;
+  const int WIN = 32 * P::E;
+  const int W = WIN - 2 * T;
+  TBArgs a;
+  a.src = src;
+  a.dst = dst;
+  a.N = c->geo.N;
+  a.r = c->r;
+  a.rf = c->rf;
+  a.T = T;
+  a.steps = steps;
+  a.ntiles = (c->geo.N + W - 1) / W;
+  a.st = c->dstat;
+  const size_t smem = smem_bytes<MODE>();
+  if (cudaFuncSetAttribute(k_tblock<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    return HEAT_ECUDA;
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tblock<MODE>, kWarps * 32, smem) != cudaSuccess ||
+      per_sm < 1)
+    return HEAT_ECUDA;
+  int64_t grid = (a.ntiles + kWarps - 1) / kWarps;
+  const int64_t cap = (int64_t)per_sm * c->sms;
+  if (grid > cap) grid = cap;
+  if (grid < 1) grid = 1;
+  k_tblock<MODE><<<(int)grid, kWarps * 32, smem, c->stream>>>(a);
+  return cuda_status(cudaGetLastError());
+}
+
+}  // namespace
+
+int tblock_window(int dtype) { return dtype == HEAT_F32C ? 32 * TB<2>::E : 32 * TB<0>::E; }
+
+int run_tblock(heat_ctx *c, int64_t nt) {
+  const int mode = c->dtype == HEAT_F32C ? 2 : (c->arith == HEAT_ARITH_FMA ? 1 : 0);
+  int T = c->T > 0 ? c->T : (c->dtype == HEAT_F32C ? 8 : 4);
+  const int WIN = tblock_window(c->dtype);
+  if (2 * T >= WIN) return HEAT_EINVAL;
+  c->last_T = T;
+  for (int64_t done = 0; done < nt;) {
+    const int steps = (int)(nt - done < T ? nt - done : T);
+    const void *src = c->buf[c->cur];
+    void *dst = c->buf[c->cur ^ 1];
+    const int rc = mode == 0 ? launch_tb<0>(c, src, dst, T, steps)
+                   : mode == 1 ? launch_tb<1>(c, src, dst, T, steps)
+                               : launch_tb<2>(c, src, dst, T, steps);
+    if (rc != HEAT_OK) return rc;
+    c->cur ^= 1;
+    c->steps += steps;
+    c->last_launches += 1;
+    done += steps;
+  }
+  return HEAT_OK;
+}
+
 }  // namespace heat

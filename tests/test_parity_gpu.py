@@ -17,8 +17,8 @@ from paper_2307_01117_gb300 import workloads
 
 pytestmark = pytest.mark.gpu
 
-FORMS_F64 = [("plain", 0), ("persist", 0)]
-FORMS_F32C = [("plain", 0), ("persist", 0)]
+FORMS_F64 = [("plain", 0), ("persist", 0), ("tblock", 1), ("tblock", 4), ("tblock", 7), ("tblock", 64)]
+FORMS_F32C = [("plain", 0), ("persist", 0), ("tblock", 1), ("tblock", 8), ("tblock", 13), ("tblock", 64)]
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -168,3 +168,30 @@ def test_argument_errors():
             H.heat_set_arith(h.ctx, 5)
         H.heat_run(h.ctx, 0)
         assert h.steps == 0
+
+
+@pytest.mark.parametrize("T", [2, 5, 16])
+def test_tblock_restart_matches_one_run_f64(T):
+    """Binary64: any split of the steps into runs and blocks gives the same bits."""
+    u0 = workloads.uniform(70001, 12, -1, 1)
+    a = run_gpu(u0, 1, 0.45, 50, "tblock", T, chunks=[11, 39])
+    b = run_gpu(u0, 1, 0.45, 50, "plain", 0)
+    assert same_bits(a, b)
+
+
+def test_tblock_default_depth_runs():
+    u0 = workloads.uniform(5000, 2, -1, 1)
+    with H.Heat(5000, 1, 0.3, 1.0, 1.0, form="tblock") as h:
+        h.set(u0).run(9)
+        got = h.get()
+        info = H.heat_last_run(h.ctx)
+    assert info["form"] == "tblock" and info["T"] >= 1
+    assert same_bits(got, oracle.run(u0, 0.3, 9))
+
+
+def test_tblock_rejects_depth_beyond_window():
+    with H.Heat(1000, 1, 0.3, 1.0, 1.0, form="tblock", T=64) as h:
+        h.set(np.zeros(1000)).run(3)           # 2T < window: fine
+        with pytest.raises(H.HeatError) as e:
+            H.heat_set_form(h.ctx, 2, 65)         # beyond the library's maximum depth
+        assert e.value.code == H.HEAT_EINVAL
