@@ -139,6 +139,26 @@ int heat_set_form(heat_ctx *c, int form, int T);
  * segments.  The result does not depend on this choice. */
 int heat_set_segments(heat_ctx *c, int segments);
 
+/* Binary64 with HEAT_ARITH_EXACT, temporal-blocking form: compute `share` of
+ * every 32 tiles with integer-pipe binary64 arithmetic instead of the FP64 unit
+ * (0..32).  GB300's FP64 unit runs at 1/64 of the FP32 rate; the integer pipes
+ * are idle during the binary64 update, so splitting the tiles between the two
+ * raises throughput.  Both paths give the correctly rounded IEEE result, so the
+ * state is bitwise the same for every share; points outside the integer
+ * routines' domain (subnormal or non-finite values) are recomputed on the FP64
+ * unit. */
+int heat_set_emulation(heat_ctx *c, int share);
+
+/* Binary64 with HEAT_ARITH_EXACT, temporal-blocking form, tiles left on the
+ * FP64 unit: move part of each point's update to the integer pipes.  level 0:
+ * all four operations (fma for ul - 2u, add, multiply by r, add) on the FP64
+ * unit; 1: the multiply by r on the integer pipes (3 FP64 operations per
+ * point; for r a power of two the product only moves the exponent); 1 + j
+ * (j = 1..16): also the final add, for j/16 of the points (2 FP64 operations
+ * there).  Bitwise the same state for every level (every operation is the
+ * correctly rounded IEEE result either way). */
+int heat_set_split(heat_ctx *c, int level);
+
 /* Select the rounding reading for HEAT_F64 (heat_arith).  HEAT_F32C ignores it. */
 int heat_set_arith(heat_ctx *c, int arith);
 

@@ -11,6 +11,8 @@ using heat::DevStatus;
 namespace {
 
 constexpr int64_t kStageElems = int64_t(1) << 22;  // binary64 staging chunk for HEAT_F32C transfers (32 MiB)
+constexpr int kDefaultEmulShare = 0;               // tiles of 32 on the integer pipes by default
+constexpr int kDefaultSplit = 0;                   // per-point FP64/integer split level by default
 
 bool is_finite(double x) { return isfinite(x) != 0; }
 
@@ -26,6 +28,7 @@ void free_ctx(heat_ctx *c) {
   if (c->seg_start) cudaFree(c->seg_start);
   if (c->partials) cudaFree(c->partials);
   if (c->hsum) cudaFreeHost(c->hsum);
+  if (c->tile_counter) cudaFree(c->tile_counter);
   if (c->own_stream) cudaStreamDestroy(c->own_stream);
   free(c);
 }
@@ -78,6 +81,8 @@ int heat_create(heat_ctx **out, int64_t nx, int32_t np, double k, double dt, dou
   c->wait_ns = 2000000000LL;
   c->inj_segment = -1;
   c->inj_step = 0;
+  heat_set_emulation(c, kDefaultEmulShare);
+  heat_set_split(c, kDefaultSplit);
   int rc = HEAT_OK;
   if (cudaGetDevice(&c->device) != cudaSuccess ||
       cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess) {
@@ -98,6 +103,8 @@ int heat_create(heat_ctx **out, int64_t nx, int32_t np, double k, double dt, dou
   if (rc == HEAT_OK && cudaMalloc((void **)&c->partials, sizeof(double) * (heat::kSumBlocks + 1)) != cudaSuccess)
     rc = HEAT_ENOMEM;
   if (rc == HEAT_OK && cudaMallocHost((void **)&c->hsum, sizeof(double)) != cudaSuccess) rc = HEAT_ENOMEM;
+  if (rc == HEAT_OK && cudaMalloc((void **)&c->tile_counter, sizeof(unsigned long long)) != cudaSuccess)
+    rc = HEAT_ENOMEM;
   if (rc == HEAT_OK) {
     for (int i = 0; i < 2 && rc == HEAT_OK; ++i)
       if (cudaMemsetAsync(c->buf[i], 0, (size_t)N * elem, c->stream) != cudaSuccess) rc = HEAT_ECUDA;
@@ -241,6 +248,23 @@ int heat_set_form(heat_ctx *c, int form, int T) {
   if (T < 0 || T > heat::kMaxT) return HEAT_EINVAL;
   c->form = form;
   c->T = T;
+  return HEAT_OK;
+}
+
+int heat_set_split(heat_ctx *c, int level) {
+  if (!c || level < 0 || level > 17) return HEAT_EINVAL;
+  c->split_level = level;
+  return HEAT_OK;
+}
+
+int heat_set_emulation(heat_ctx *c, int share) {
+  if (!c || share < 0 || share > 32) return HEAT_EINVAL;
+  c->emul_share = share;
+  // spread `share` set bits evenly over 32 positions
+  unsigned mask = 0;
+  for (int i = 0; i < 32; ++i)
+    if (((i + 1) * share) / 32 > (i * share) / 32) mask |= 1u << i;
+  c->emul_mask = mask;
   return HEAT_OK;
 }
 

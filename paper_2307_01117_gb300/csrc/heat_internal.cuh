@@ -69,7 +69,11 @@ struct heat_ctx {
   int last_form;                 // form used by the last heat_run
   int last_T;                    // temporal block depth used by the last heat_run
   int64_t last_launches;         // stencil kernel launches queued by the last heat_run
+  int emul_share;                // tiles of 32 computed on the integer pipes (binary64, exact reading)
+  unsigned emul_mask;            // the same as a bit mask over tile index mod 32
+  int split_level;               // per-point split of the binary64 update between FP64 unit and integer pipes
   double *partials;              // reduction scratch, device
+  unsigned long long *tile_counter;  // dynamic tile counter of the temporal-blocking form, device
   double *hsum;                  // pinned host word for heat_sum
   int64_t wait_ns;
   int32_t inj_segment;

@@ -18,8 +18,18 @@
 // are one compensation block, stored as RN(h + l) (the library's HEAT_F32C
 // definition).
 //
+// Binary64, exact reading: a share of the tiles (chosen by a 32-bit mask over
+// tile index mod 32) is computed with the integer-pipe binary64 routines of
+// dp_emul.cuh instead of the FP64 unit; both give the correctly rounded IEEE
+// result, so the bits do not depend on the share.  If any point of an emulated
+// tile leaves the routines' domain, the warp recomputes that tile on the FP64
+// unit from its staged window.
+//
 // Algorithmic HBM traffic per launch: N points read + N written (16 B per point
 // per T steps in binary64, 8 B in binary32); the halo re-read adds WIN/W.
+#include <string.h>
+
+#include "dp_emul.cuh"
 #include "heat_internal.cuh"
 #include "stencil_ops.cuh"
 
@@ -88,6 +98,50 @@ struct TBf64 {
       Rcur = Rn;
     }
   }
+  // The step with its multiply (and, for registers k whose bit is set in
+  // add_mask, its final add) done by the integer-pipe routines; the two
+  // differences stay on the FP64 unit.  Exact reading only.  The FP64 unit then
+  // issues 3 (or 2) operations per point instead of 4.
+  static __device__ __forceinline__ void step_split(Reg &R, int lane, const emul::Mul &m, unsigned add_mask,
+                                                    bool &bad) {
+    const int lm = (lane + 31) & 31, lp = (lane + 1) & 31;
+    double Lprev = __shfl_sync(kFull, R.x[0], lm);
+    double Rcur = __shfl_sync(kFull, R.x[0], lp);
+#pragma unroll
+    for (int k = 0; k < E; ++k) {
+      const double Lk = k == 0 ? Lprev : __shfl_sync(kFull, R.x[k], lm);
+      const double Rn = k + 1 < E ? __shfl_sync(kFull, R.x[k + 1], lp) : Rcur;
+      const double left = lane == 0 ? Lprev : Lk;
+      const double right = lane == 31 ? Rn : Rcur;
+      const double t1 = __fma_rn(-2.0, R.x[k], left);
+      const double t2 = __dadd_rn(t1, right);
+      const uint64_t t3 = emul::mul(m, (uint64_t)__double_as_longlong(t2), bad);
+      if ((add_mask >> k) & 1u)
+        R.x[k] = __longlong_as_double((long long)emul::add((uint64_t)__double_as_longlong(R.x[k]), t3, bad));
+      else
+        R.x[k] = __dadd_rn(R.x[k], __longlong_as_double((long long)t3));
+      Lprev = Lk;
+      Rcur = Rn;
+    }
+  }
+  // The same step with the integer-pipe binary64 routines (exact reading only).
+  static __device__ __forceinline__ void step_emul(Reg &R, int lane, const emul::Mul &m, bool &bad) {
+    const int lm = (lane + 31) & 31, lp = (lane + 1) & 31;
+    double Lprev = __shfl_sync(kFull, R.x[0], lm);
+    double Rcur = __shfl_sync(kFull, R.x[0], lp);
+#pragma unroll
+    for (int k = 0; k < E; ++k) {
+      const double Lk = k == 0 ? Lprev : __shfl_sync(kFull, R.x[k], lm);
+      const double Rn = k + 1 < E ? __shfl_sync(kFull, R.x[k + 1], lp) : Rcur;
+      const double left = lane == 0 ? Lprev : Lk;
+      const double right = lane == 31 ? Rn : Rcur;
+      const uint64_t v = emul::eq2_exact((uint64_t)__double_as_longlong(left), (uint64_t)__double_as_longlong(R.x[k]),
+                                         (uint64_t)__double_as_longlong(right), m, bad);
+      R.x[k] = __longlong_as_double((long long)v);
+      Lprev = Lk;
+      Rcur = Rn;
+    }
+  }
 };
 template <>
 struct TB<0> : TBf64<0> {};
@@ -132,6 +186,11 @@ struct TB<2> {
   }
 };
 
+template <int MODE>
+struct HasEmul {
+  static constexpr bool value = MODE == 0;
+};
+
 struct TBArgs {
   const void *src;
   void *dst;
@@ -142,6 +201,11 @@ struct TBArgs {
   int steps;    // steps this launch (<= T)
   int64_t ntiles;
   DevStatus *st;
+  unsigned emul_mask;  // bit (tile mod 32) set: compute the tile on the integer pipes
+  unsigned long long *tile_counter;  // launch-wide tile counter, zero at launch
+  int split;           // other tiles: multiply (and masked final adds) on the integer pipes
+  unsigned add_mask;   // registers k whose final add also goes to the integer pipes
+  emul::Mul m;         // prepared multiplier r (valid when emul_mask != 0)
 };
 
 template <int MODE>
@@ -162,8 +226,6 @@ __global__ void __launch_bounds__(kWarps * 32) k_tblock(TBArgs a) {
   T *dst = (T *)a.dst;
   const int64_t N = a.N;
   const int W = WIN - 2 * a.T;
-  const int64_t warp = ((int64_t)blockIdx.x * kWarps + wib);
-  const int64_t nwarps = (int64_t)gridDim.x * kWarps;
 
   if (lane == 0) {
     mbar_init(&bar[0], 1);
@@ -189,14 +251,24 @@ __global__ void __launch_bounds__(kWarps * 32) k_tblock(TBArgs a) {
 
   unsigned phase0 = 0u, phase1 = 0u;  // mbarrier phase parity per staging buffer
   int b = 0;
-  if (warp < a.ntiles) issue(warp, 0);
-  for (int64_t tile = warp; tile < a.ntiles; tile += nwarps) {
-    const int64_t next = tile + nwarps;
+  // Tiles are claimed dynamically from a launch-wide counter, zeroed before the
+  // launch (one atomic per tile, by lane 0), so warps that draw slower tiles do
+  // not hold up the rest.
+  auto claim = [&]() -> int64_t {
+    unsigned long long t = 0;
+    if (lane == 0) t = atomicAdd(a.tile_counter, 1ull);
+    return (int64_t)__shfl_sync(kFull, t, 0);
+  };
+  int64_t tile = claim();
+  if (tile < a.ntiles) issue(tile, 0);
+  for (; tile < a.ntiles;) {
+    const int64_t next = claim();
     __syncwarp();
     if (next < a.ntiles) issue(next, b ^ 1);
     const int64_t ws = window_start(tile);
     typename P::Reg R;
-    if (tma_ok(ws)) {
+    const bool staged = tma_ok(ws);
+    if (staged) {
       // every lane observes the barrier; the loop exits for the whole warp at once
       bool done = false;
       for (long long spin = 0; spin < kMaxWaitSpins && !done; ++spin)
@@ -209,18 +281,38 @@ __global__ void __launch_bounds__(kWarps * 32) k_tblock(TBArgs a) {
         return;
       }
       if (b) phase1 ^= 1u; else phase0 ^= 1u;
-      const T *sb = buf0 + b * BUF + (int)(ws - (ws & ~(int64_t)(P::kAlign - 1)));
+    }
+    const T *sb = buf0 + b * BUF + (int)(ws - (ws & ~(int64_t)(P::kAlign - 1)));
+    auto load_window = [&]() {
+      if (staged) {
 #pragma unroll
-      for (int k = 0; k < E; ++k) P::load(R, k, sb[32 * k + lane]);
-    } else {
+        for (int k = 0; k < E; ++k) P::load(R, k, sb[32 * k + lane]);
+      } else {
 #pragma unroll
-      for (int k = 0; k < E; ++k) {
-        int64_t g = (ws + 32 * k + lane) % N;
-        if (g < 0) g += N;
-        P::load(R, k, src[g]);
+        for (int k = 0; k < E; ++k) {
+          int64_t g = (ws + 32 * k + lane) % N;
+          if (g < 0) g += N;
+          P::load(R, k, src[g]);
+        }
+      }
+    };
+    load_window();
+    bool dp = true;
+    if constexpr (HasEmul<MODE>::value) {
+      if ((a.emul_mask >> (unsigned)(tile & 31)) & 1u) {
+        bool bad = false;
+        for (int s = 0; s < a.steps; ++s) P::step_emul(R, lane, a.m, bad);
+        dp = __any_sync(kFull, bad);
+        if (dp) load_window();  // some point left the routines' domain: redo on the FP64 unit
+      } else if (a.split) {
+        bool bad = false;
+        for (int s = 0; s < a.steps; ++s) P::step_split(R, lane, a.m, a.add_mask, bad);
+        dp = __any_sync(kFull, bad);
+        if (dp) load_window();
       }
     }
-    for (int s = 0; s < a.steps; ++s) P::step(R, lane, a.r, a.rf);
+    if (dp)
+      for (int s = 0; s < a.steps; ++s) P::step(R, lane, a.r, a.rf);
     // store the W exact points of the window: indices T .. WIN-1-T
 #pragma unroll
     for (int k = 0; k < E; ++k) {
@@ -229,6 +321,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_tblock(TBArgs a) {
       if (i >= a.T && i < WIN - a.T && g < N) dst[g] = P::store(R, k);
     }
     b ^= 1;
+    tile = next;
   }
 }
 
@@ -253,6 +346,22 @@ int launch_tb(heat_ctx *c, const void *src, void *dst, int T, int steps) {
   a.steps = steps;
   a.ntiles = (c->geo.N + W - 1) / W;
   a.st = c->dstat;
+  uint64_t rbits;
+  memcpy(&rbits, &c->r, sizeof(rbits));
+  const int rexp = (int)((rbits >> 52) & 2047);
+  // the routines take a normal, nonzero multiplier; otherwise every tile uses the FP64 unit
+  a.emul_mask = (MODE == 0 && rexp >= 1 && rexp <= 2046) ? c->emul_mask : 0u;
+  a.m = emul::prepare_mul(rbits);
+  a.tile_counter = c->tile_counter;
+  // split_level 0: every FP64-unit tile keeps 4 FP64 operations per point;
+  // 1: the multiply goes to the integer pipes (3 per point); 1 + j (j = 1..16):
+  // the final add too, for j of the 16 registers spread evenly (those points
+  // need 2 FP64 operations)
+  a.split = MODE == 0 && rexp >= 1 && rexp <= 2046 && c->split_level > 0;
+  const int j = c->split_level > 1 ? c->split_level - 1 : 0;
+  a.add_mask = 0u;
+  for (int i = 0; i < 16; ++i)
+    if (((i + 1) * j) / 16 > (i * j) / 16) a.add_mask |= 1u << i;
   const size_t smem = smem_bytes<MODE>();
   if (cudaFuncSetAttribute(k_tblock<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
     return HEAT_ECUDA;
@@ -264,6 +373,7 @@ int launch_tb(heat_ctx *c, const void *src, void *dst, int T, int steps) {
   const int64_t cap = (int64_t)per_sm * c->sms;
   if (grid > cap) grid = cap;
   if (grid < 1) grid = 1;
+  if (cudaMemsetAsync(c->tile_counter, 0, sizeof(unsigned long long), c->stream) != cudaSuccess) return HEAT_ECUDA;
   k_tblock<MODE><<<(int)grid, kWarps * 32, smem, c->stream>>>(a);
   return cuda_status(cudaGetLastError());
 }

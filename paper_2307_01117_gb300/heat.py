@@ -49,6 +49,8 @@ _PROTOS = {
     "heat_set_form": (_int, [_vp, _int, _int]),
     "heat_set_arith": (_int, [_vp, _int]),
     "heat_set_segments": (_int, [_vp, _int]),
+    "heat_set_emulation": (_int, [_vp, _int]),
+    "heat_set_split": (_int, [_vp, _int]),
     "heat_sum": (_int, [_vp, ctypes.POINTER(_d)]),
     "heat_steps": (_int, [_vp, ctypes.POINTER(_i64)]),
     "heat_last_run": (_int, [_vp, ctypes.POINTER(_int), ctypes.POINTER(_int), ctypes.POINTER(_i64),
@@ -156,6 +158,14 @@ def heat_set_form(ctx: int, form, T: int = 0) -> None:
 
 def heat_set_segments(ctx: int, segments: int) -> None:
     _check(lib().heat_set_segments(ctx, int(segments)), "heat_set_segments")
+
+
+def heat_set_emulation(ctx: int, share: int) -> None:
+    _check(lib().heat_set_emulation(ctx, int(share)), "heat_set_emulation")
+
+
+def heat_set_split(ctx: int, level: int) -> None:
+    _check(lib().heat_set_split(ctx, int(level)), "heat_set_split")
 
 
 def heat_set_arith(ctx: int, arith: int) -> None:

@@ -1,0 +1,85 @@
+"""Binary64 tiles computed on the integer pipes (heat_set_emulation) give
+bitwise the oracle's result for every share, including data that leaves the
+integer routines' domain (zeros, subnormals) and power-of-two and general r."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2307_01117_gb300 import heat as H
+from paper_2307_01117_gb300 import workloads
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2307_01117_gb300 import build
+    build.build()
+
+
+def run(u0, r, nt, T, share):
+    with H.Heat(len(u0), 1, r, 1.0, 1.0, form="tblock", T=T) as h:
+        H.heat_set_emulation(h.ctx, share)
+        h.set(u0).run(nt)
+        return h.get()
+
+
+def bits(a):
+    return np.asarray(a).view(np.uint64)
+
+
+@pytest.mark.parametrize("share", [0, 1, 8, 16, 31, 32])
+@pytest.mark.parametrize("r", [0.25, 0.5, 0.3, 0.123456789])
+def test_every_share_is_bitwise_the_oracle(share, r):
+    n = 3 * 4096 + 17
+    u0 = workloads.uniform(n, 90 + share, -1, 1)
+    ref = oracle.run(u0, r, 21)
+    assert np.array_equal(bits(run(u0, r, 21, 7, share)), bits(ref))
+
+
+@pytest.mark.parametrize("share", [16, 32])
+def test_paper_ramp_with_zero_second_differences(share):
+    u0 = workloads.ramp(4000)
+    ref = oracle.run(u0, 0.5, 100)
+    assert np.array_equal(bits(run(u0, 0.5, 100, 4, share)), bits(ref))
+
+
+@pytest.mark.parametrize("share", [32])
+def test_out_of_domain_values_fall_back(share):
+    n = 8192
+    u0 = workloads.uniform(n, 3, -1, 1)
+    u0[100:140] = 0.0
+    u0[500:520] = 5e-310           # subnormal
+    u0[900] = -0.0
+    u0[2000:2010] = 1e-300         # results go subnormal after a few steps
+    ref = oracle.run(u0, 0.37, 12)
+    assert np.array_equal(bits(run(u0, 0.37, 12, 4, share)), bits(ref))
+
+
+def test_constant_field_stays_constant():
+    u0 = np.full(10000, 0.7)
+    assert np.array_equal(run(u0, 0.25, 30, 8, 32), u0)
+
+
+@pytest.mark.parametrize("split", [1, 2, 9, 17])
+@pytest.mark.parametrize("r", [0.25, 0.3])
+def test_split_levels_are_bitwise_the_oracle(split, r):
+    n = 2 * 4096 + 333
+    u0 = workloads.uniform(n, 7 + split, -1, 1)
+    with H.Heat(n, 1, r, 1.0, 1.0, form="tblock", T=5) as h:
+        H.heat_set_split(h.ctx, split)
+        h.set(u0).run(23)
+        got = h.get()
+    assert np.array_equal(bits(got), bits(oracle.run(u0, r, 23)))
+
+
+def test_split_with_out_of_domain_values():
+    n = 8192
+    u0 = workloads.uniform(n, 4, -1, 1)
+    u0[10:30] = 0.0
+    u0[300:310] = 4e-310
+    with H.Heat(n, 1, 0.3, 1.0, 1.0, form="tblock", T=4) as h:
+        H.heat_set_split(h.ctx, 17)
+        h.set(u0).run(10)
+        got = h.get()
+    assert np.array_equal(bits(got), bits(oracle.run(u0, 0.3, 10)))
