@@ -1,26 +1,41 @@
 """Benchmark of the periodic 1D heat stencil (Eq. 2, Section 2) on GB300.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--form auto|plain|persist|tblock]
-                    [--T depth] [--dtype f64|f32c] [--workload ring-2^28-f64|...] [--impl ours|reference]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
+                    [--form auto|plain|persist|tblock] [--T depth] [--arith exact|fma]
+                    [--split L] [--emul S] [--impl ours|reference]
 
-One bench step is one pass of the whole hot path over one batch of synthetic
-input: load the initial state from a device-resident copy (heat_set_device),
-advance nt steps (heat_run), take the FP64 conservation sum (heat_sum).  The
-metric is GLUP/s = ring points x time steps / second (the paper's "cells
-processed per second", Section 6).  Rank 0 prints one JSON line.
+Workloads (all synthetic, seeded; the paper's own workload is synthetic too):
+  ring-2^28-f64   (default) one ring, np = 256 x nx = 2^20, nt = 1000, r = 0.25,
+                  u0 = U[0,1) + sin(2 pi 3 g / N)
+  ring-1e6-f64    the paper's shape (Section 6): 10^6 points, 1000 steps, u0 = g
+  ring-4000-f64   np = 4 x nx = 1000, nt = 100, r = 0.5, u0 = g
+  ring-2^25-f64   profiling case (still larger than L2)
+  ring-2^28-f32c  binary32 compensated state, u0 = sum of modes 1, 7, 64
+  batch-4096-f64  4096 independent rings, N log-uniform in [1e3, 1e6], np in
+                  {1,2,4,8,16}, nt uniform in [100, 5000], r uniform in
+                  [0.05, 0.5], u0 = U[-1,1) (seed 1), one persistent launch
+  batch-256-f64   the first 256 rings of the same table
 
-Under torchrun (N > 1) every rank runs its own independent replica of the
-workload on its own GPU (the ring is not sharded across GPUs): weak scaling, no
+One bench step is one pass of the whole hot path over one batch of input:
+load the initial state from a device-resident copy, advance every ring its nt
+steps, take the FP64 conservation sum (single ring) or synchronise (batch).
+value = ring point-steps / second (GLUP/s, the paper's "cells processed per
+second", Section 6), timed with CUDA events on the work's stream, 3+ warm-ups,
+inputs larger than L2.  `e2e` is the same metric through the C ABI with host
+buffers: the initial state is copied in from pinned host memory and the final
+state read back inside the timed region.
+
+Under torchrun (N > 1) every rank runs its own independent replica on its own
+GPU (replicas only: the ring is not sharded across GPUs): weak scaling, no
 data-path collective; `value` is all ranks' point-steps over the slowest rank's
 time.  ``--impl reference`` times the CPU oracle (single thread) on a bounded
-sample of the same workload instead.
+sample of the workload instead.  Rank 0 prints one JSON line.
 """
 from __future__ import annotations
 
 import argparse
 import hashlib
 import json
-import math
 import os
 import statistics
 import subprocess
@@ -33,29 +48,26 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-METRIC = "FP64 GLUP/s (ring point-steps per second)"
-METRIC_F32C = "binary32-compensated GLUP/s (ring point-steps per second)"
 UNIT = "GLUP/s"
+METRIC = {"f64": "FP64 GLUP/s (ring point-steps per second)",
+          "f32c": "binary32-compensated GLUP/s (ring point-steps per second)"}
 
-# name -> (nx, np, nt, k, dt, dx, initial condition, dtype)
 WORKLOADS = {
-    # np=256 partitions x nx=2^20 points (N = 2^28, 2.1 GB per binary64 buffer), nt=1000, r=0.25,
-    # u0 = U[0,1) from PCG64 seed 0 plus the Fourier mode m=3 of amplitude 1
-    "ring-2^28-f64": dict(nx=1 << 20, np=256, nt=1000, k=0.25, dt=1.0, dx=1.0, init="uniform+mode3", dtype="f64"),
-    # the paper's shape (Section 6): 1e6 nodes, 1000 steps, u0[g] = g
-    "ring-1e6-f64": dict(nx=250000, np=4, nt=1000, k=0.25, dt=1.0, dx=1.0, init="ramp", dtype="f64"),
-    # np=4 x nx=1000, nt=100, k=0.5 (r=0.5), u0[g] = g
-    "ring-4000-f64": dict(nx=1000, np=4, nt=100, k=0.5, dt=1.0, dx=1.0, init="ramp", dtype="f64"),
-    # profiling case: np=32 x nx=2^20 (N = 2^25, 268 MB per buffer, still larger than L2), nt=20
-    "ring-2^25-f64": dict(nx=1 << 20, np=32, nt=20, k=0.25, dt=1.0, dx=1.0, init="uniform+mode3", dtype="f64"),
-    # binary32 state with the compensated update, same ring as the first, r = 0.25
-    "ring-2^28-f32c": dict(nx=1 << 20, np=256, nt=1000, k=0.25, dt=1.0, dx=1.0, init="modes1,7,64", dtype="f32c"),
+    "ring-2^28-f64": dict(kind="ring", nx=1 << 20, np=256, nt=1000, k=0.25, dt=1.0, dx=1.0, init="uniform+mode3",
+                          dtype="f64"),
+    "ring-1e6-f64": dict(kind="ring", nx=250000, np=4, nt=1000, k=0.25, dt=1.0, dx=1.0, init="ramp", dtype="f64"),
+    "ring-4000-f64": dict(kind="ring", nx=1000, np=4, nt=100, k=0.5, dt=1.0, dx=1.0, init="ramp", dtype="f64"),
+    "ring-2^25-f64": dict(kind="ring", nx=1 << 20, np=32, nt=20, k=0.25, dt=1.0, dx=1.0, init="uniform+mode3",
+                          dtype="f64"),
+    "ring-2^28-f32c": dict(kind="ring", nx=1 << 20, np=256, nt=1000, k=0.25, dt=1.0, dx=1.0, init="modes1,7,64",
+                           dtype="f32c"),
+    "batch-4096-f64": dict(kind="batch", count=4096, seed=1, dtype="f64"),
+    "batch-256-f64": dict(kind="batch", count=256, seed=1, dtype="f64"),
 }
 DEFAULT_WORKLOAD = "ring-2^28-f64"
 
-# DP instructions per point-step of the binary64 update (exact reading: fma, add, mul, add;
-# fused reading: fma, add, fma); binary32-compensated: about 14 FP32 operations.
-DP_OPS = {0: 4, 1: 3}
+# FP64-unit instructions per point-step: exact reading fma, add, mul, add; fused reading fma, add, fma
+DP_OPS = {"exact": 4, "fma": 3}
 
 
 def initial_state(w: dict) -> np.ndarray:
@@ -117,7 +129,7 @@ class ClockSampler:
             self.proc.kill()
         if self.thread:
             self.thread.join(timeout=2)
-        sm, smax, reasons = [], [], set()
+        sm, smax, power, reasons = [], [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for ln in self.lines:
             parts = [x.strip() for x in ln.split(",")]
@@ -126,18 +138,20 @@ class ClockSampler:
             try:
                 sm.append(float(parts[0]))
                 smax.append(float(parts[1]))
+                power.append(float(parts[2]))
             except ValueError:
                 continue
             for nm, v in zip(names, parts[4:8]):
                 if v.lower() == "active":
                     reasons.add(nm)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "power_w_median": statistics.median(power) if power else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
 
 
 def profile_traffic(kernel: str, workload: str, src_files: list[str]) -> float | None:
-    """DRAM bytes per launch from the committed ncu summary, if the kernel source
-    is unchanged since it was taken."""
+    """DRAM bytes per launch from the committed ncu summary (profiles/traffic.json),
+    if the kernel's source is unchanged since the counters were taken."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
@@ -154,21 +168,34 @@ def profile_traffic(kernel: str, workload: str, src_files: list[str]) -> float |
     return float(rec["dram_bytes_per_launch"])
 
 
+# ---------------------------------------------------------------------------------------------
+# CPU oracle baseline
+
 def cpu_baseline(w: dict, seconds: float = 12.0) -> dict:
     """The CPU oracle, as it stands, single-threaded on a bounded sample of the
-    workload: the first 2^22 points of the ring's initial state treated as a
-    ring of its own, stepped until about `seconds` have passed."""
+    workload, stepped until about `seconds` have passed."""
     import oracle
+    if w["kind"] == "batch":
+        from paper_2307_01117_gb300 import workloads
+        specs = workloads.ring_table(w["count"], seed=w["seed"])
+        done_pts, total, rings = 0, 0.0, 0
+        for spec in specs:
+            if total >= seconds:
+                break
+            u0 = workloads.ring_initial(spec)
+            t0 = time.perf_counter()
+            oracle.run(u0, spec.r, spec.nt)
+            total += time.perf_counter() - t0
+            done_pts += spec.n * spec.nt
+            rings += 1
+        return {"value": done_pts / total / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+                "sample": f"the first {rings} rings of the table, all their steps, {total:.1f} s on 1 host core"}
     n = min(w["nx"] * w["np"], 1 << 22)
     w2 = dict(w)
     w2["nx"], w2["np"] = n, 1
-    u0 = initial_state(w2)
+    u = initial_state(w2)
     r = oracle.coef(w["k"], w["dt"], w["dx"])
-    t0 = time.perf_counter()
-    oracle.run(u0[: min(n, 1 << 16)], r, 2)
-    steps, total = 0, 0.0
-    chunk = 4
-    u = u0
+    steps, total, chunk = 0, 0.0, 4
     while total < seconds:
         t0 = time.perf_counter()
         if w["dtype"] == "f32c":
@@ -178,22 +205,171 @@ def cpu_baseline(w: dict, seconds: float = 12.0) -> dict:
         total += time.perf_counter() - t0
         steps += chunk
     return {"value": n * steps / total / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{n} points x {steps} steps ({'binary32 compensated' if w['dtype'] == 'f32c' else 'binary64'}), "
-                      f"{total:.1f} s on 1 host core"}
+            "sample": f"first {n} points of the initial state as a ring of their own x {steps} steps "
+                      f"({'binary32 compensated' if w['dtype'] == 'f32c' else 'binary64'}), {total:.1f} s on 1 host core"}
 
 
-def run_reference(args, w: dict, rank: int, world: int) -> None:
+def run_reference(args, w: dict, rank: int) -> None:
     if rank != 0:
         return
     cb = cpu_baseline(w, seconds=max(2.0, 2.0 * args.steps))
-    line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if w["dtype"] == "f64" else "f32",
-            "data": "synthetic", "config": {"workload": args.workload, **{k: w[k] for k in ("nx", "np", "nt", "k")}},
-            "cpu_baseline": cb, "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0,
-                                        "d2h_bytes_per_step": 0}}
+    line = {"impl": "reference", "metric": METRIC[w["dtype"]], "value": cb["value"], "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": None,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if w["dtype"] == "f64" else "f32", "data": "synthetic",
+            "config": {"workload": args.workload}, "cpu_baseline": cb,
+            "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
+
+# ---------------------------------------------------------------------------------------------
+# Runners, one per workload kind: step(events), e2e_prepare/e2e_step, kernel_info, config.
+
+class RingRunner:
+    def __init__(self, args, w, H, torch, local, stream):
+        self.args, self.w, self.H, self.torch, self.stream = args, w, H, torch, stream
+        self.n = w["nx"] * w["np"]
+        self.nt = w["nt"]
+        self.point_steps = float(self.n) * self.nt
+        self.u0 = initial_state(w)
+        self.u0_dev = torch.from_numpy(self.u0).to(f"cuda:{local}")
+        arith = H.HEAT_ARITH_FMA if args.arith == "fma" else H.HEAT_ARITH_EXACT
+        self.h = H.Heat(w["nx"], w["np"], w["k"], w["dt"], w["dx"], dtype=w["dtype"], form=args.form, T=args.T,
+                        arith=arith, stream=stream)
+        if args.split:
+            H.heat_set_split(self.h.ctx, args.split)
+        if args.emul:
+            H.heat_set_emulation(self.h.ctx, args.emul)
+
+    def step(self, ev=None):
+        H, ctx = self.H, self.h.ctx
+        H.heat_set_device(ctx, self.u0_dev)
+        if ev is not None:
+            ev[0].record(self.stream)
+        H.heat_run(ctx, self.nt)
+        if ev is not None:
+            ev[1].record(self.stream)
+        H.heat_sum(ctx)  # synchronises the stream
+
+    def e2e_prepare(self):
+        torch = self.torch
+        self.host_in = torch.empty(self.n, dtype=torch.float64, pin_memory=True).numpy()
+        self.host_in[:] = self.u0
+        self.host_out = torch.empty(self.n, dtype=torch.float64, pin_memory=True).numpy()
+
+    def e2e_step(self):
+        H, ctx = self.H, self.h.ctx
+        H.heat_set(ctx, self.host_in)
+        H.heat_run(ctx, self.nt)
+        H.heat_sum(ctx)
+        H.heat_get(ctx, self.host_out)
+
+    def e2e_bytes(self):
+        return self.n * 8, self.n * 8
+
+    def kernel_info(self, run_ms):
+        last = self.H.heat_last_run(self.h.ctx)
+        form = last["form"]
+        launches = max(1, last["launches"])
+        name = {"plain": "k_plain_f64" if self.w["dtype"] == "f64" else "k_plain_f32c", "persist": "k_persist",
+                "tblock": "k_tblock"}[form]
+        src = {"k_plain_f64": "k_plain.cu", "k_plain_f32c": "k_plain.cu", "k_persist": "k_persist.cu",
+               "k_tblock": "k_tblock.cu"}[name]
+        srcs = [f"paper_2307_01117_gb300/csrc/{src}", "paper_2307_01117_gb300/csrc/stencil_ops.cuh"]
+        if name == "k_tblock":
+            srcs.append("paper_2307_01117_gb300/csrc/tb_core.cuh")
+        steps_per_launch = self.nt / launches
+        elem = 8.0 if self.w["dtype"] == "f64" else 4.0
+        # every point read once and written once per launch; the persistent form
+        # streams the ring through HBM once per step
+        alg_bytes = 2.0 * elem * self.n * (steps_per_launch if form == "persist" else 1.0)
+        return {"kernel": name, "src": srcs, "launches": launches, "launch_ms": statistics.mean(run_ms) / launches,
+                "point_steps_per_launch": self.n * steps_per_launch, "alg_bytes_per_launch": alg_bytes,
+                "form": form, "T": last["T"], "segments": last["segments"] if form != "plain" else None}
+
+    def config(self):
+        w = self.w
+        return {"workload": self.args.workload, "nx": w["nx"], "np": w["np"], "N": self.n, "nt": self.nt,
+                "k": w["k"], "dt": w["dt"], "dx": w["dx"], "init": w["init"], "arith": self.args.arith,
+                "split": self.args.split, "emul": self.args.emul,
+                "l2": "inputs larger than L2 (no flush needed)" if self.n * 8 > 2 * 135e6 else "L2-resident ring"}
+
+    def close(self):
+        self.h.close()
+
+
+class BatchRunner:
+    def __init__(self, args, w, H, torch, local, stream):
+        from paper_2307_01117_gb300 import workloads
+        self.args, self.w, self.H, self.torch, self.stream = args, w, H, torch, stream
+        self.specs = workloads.ring_table(w["count"], seed=w["seed"])
+        self.inits = [workloads.ring_initial(s) for s in self.specs]
+        self.n_total = sum(s.n for s in self.specs)
+        self.point_steps = float(sum(s.n * s.nt for s in self.specs))
+        dt = H.HEAT_F64 if w["dtype"] == "f64" else H.HEAT_F32C
+        self.b = H.heat_batch_create(sum(s.n + 64 for s in self.specs), dt)
+        H.heat_batch_set_stream(self.b, stream)
+        self.ids = [H.heat_batch_add(self.b, s.nx, s.np_, s.r, 1.0, 1.0, s.nt, u) for s, u in
+                    zip(self.specs, self.inits)]
+        if args.T:
+            H.heat_batch_set_tuning(self.b, args.T, 0)
+            self.tuned = (args.T, 16384)
+        else:
+            self.tuned = H.heat_batch_autotune(self.b)
+        H.heat_batch_save(self.b)
+
+    def step(self, ev=None):
+        H = self.H
+        H.heat_batch_restore(self.b)
+        if ev is not None:
+            ev[0].record(self.stream)
+        H.heat_batch_run(self.b, 0)
+        if ev is not None:
+            ev[1].record(self.stream)
+        H.heat_batch_sync(self.b)
+
+    def e2e_prepare(self):
+        torch = self.torch
+        self.host_in = [torch.from_numpy(u).pin_memory().numpy() for u in self.inits]
+        self.host_out = [torch.empty(s.n, dtype=torch.float64, pin_memory=True).numpy() for s in self.specs]
+
+    def e2e_step(self):
+        H = self.H
+        for rid in self.ids:
+            H.heat_batch_remove(self.b, rid)
+        self.ids = [H.heat_batch_add(self.b, s.nx, s.np_, s.r, 1.0, 1.0, s.nt, u) for s, u in
+                    zip(self.specs, self.host_in)]
+        H.heat_batch_run(self.b, 0)
+        for rid, s, out in zip(self.ids, self.specs, self.host_out):
+            H.heat_batch_get(self.b, rid, s.n, out)
+
+    def e2e_bytes(self):
+        return self.n_total * 8, self.n_total * 8
+
+    def kernel_info(self, run_ms):
+        T = self.tuned[0]
+        elem = 8.0 if self.w["dtype"] == "f64" else 4.0
+        # every point read and written once per T-step level
+        level_points = sum(-(-s.nt // T) * s.n for s in self.specs)
+        return {"kernel": "k_batch", "src": ["paper_2307_01117_gb300/csrc/k_batch.cu",
+                                             "paper_2307_01117_gb300/csrc/tb_core.cuh"],
+                "launches": 1, "launch_ms": statistics.mean(run_ms), "point_steps_per_launch": self.point_steps,
+                "alg_bytes_per_launch": 2.0 * elem * level_points, "form": "batch", "T": T,
+                "segments": self.tuned[1]}
+
+    def config(self):
+        ns = [s.n for s in self.specs]
+        return {"workload": self.args.workload, "rings": len(self.specs), "points": self.n_total,
+                "point_steps": self.point_steps, "n_min": min(ns), "n_max": max(ns),
+                "nt_range": [min(s.nt for s in self.specs), max(s.nt for s in self.specs)],
+                "tuning": {"T": self.tuned[0], "seg_points": self.tuned[1]},
+                "l2": "inputs larger than L2 (no flush needed)"}
+
+    def close(self):
+        self.H.heat_batch_destroy(self.b)
+
+
+# ---------------------------------------------------------------------------------------------
 
 def main() -> int:
     ap = argparse.ArgumentParser()
@@ -204,6 +380,8 @@ def main() -> int:
     ap.add_argument("--form", default="auto", choices=["auto", "plain", "persist", "tblock"])
     ap.add_argument("--T", type=int, default=0)
     ap.add_argument("--arith", default="exact", choices=["exact", "fma"])
+    ap.add_argument("--split", type=int, default=0)
+    ap.add_argument("--emul", type=int, default=0)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -216,7 +394,7 @@ def main() -> int:
     local = int(os.environ.get("LOCAL_RANK", "0"))
 
     if args.impl == "reference":
-        run_reference(args, w, rank, world)
+        run_reference(args, w, rank)
         return 0
 
     import torch
@@ -231,32 +409,23 @@ def main() -> int:
     if not os.path.exists(H.LIB_PATH):
         hbuild.build()
 
-    n = w["nx"] * w["np"]
-    nt = w["nt"]
-    arith = H.HEAT_ARITH_FMA if args.arith == "fma" else H.HEAT_ARITH_EXACT
-    u0 = initial_state(w)
     stream = torch.cuda.Stream()
-    u0_dev = torch.from_numpy(u0).to(f"cuda:{local}")
-    h = H.Heat(w["nx"], w["np"], w["k"], w["dt"], w["dx"], dtype=w["dtype"], form=args.form, T=args.T,
-               arith=arith, stream=stream)
-    ctx = h.ctx
+    runner = (RingRunner if w["kind"] == "ring" else BatchRunner)(args, w, H, torch, local, stream)
 
     def barrier():
         torch.cuda.synchronize()
         if dist is not None:
             dist.barrier()
 
-    def step(ev=None):
-        H.heat_set_device(ctx, u0_dev)
-        if ev is not None:
-            ev[0].record(stream)
-        H.heat_run(ctx, nt)
-        if ev is not None:
-            ev[1].record(stream)
-        return H.heat_sum(ctx)   # synchronises the stream
+    def max_over_ranks(x: float) -> float:
+        if dist is None:
+            return x
+        t = torch.tensor([x], device=f"cuda:{local}")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
 
     for _ in range(args.warmup):
-        step()
+        runner.step()
     barrier()
 
     clocks = ClockSampler(local)
@@ -266,105 +435,72 @@ def main() -> int:
     barrier()
     t_start.record(stream)
     for i in range(args.steps):
-        step(evs[i])
+        runner.step(evs[i])
     t_end.record(stream)
     barrier()
     clk = clocks.stop()
-    ms_total = t_start.elapsed_time(t_end)
+    ms_max = max_over_ranks(t_start.elapsed_time(t_end))
     run_ms = [a.elapsed_time(b) for a, b in evs]
+    value = world * runner.point_steps * args.steps / (ms_max * 1e-3) / 1e9
 
-    ms_max = ms_total
-    if dist is not None:
-        t = torch.tensor([ms_total], device=f"cuda:{local}")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_max = float(t.item())
-    ms_per_step = ms_max / args.steps
-    point_steps = float(n) * nt
-    value = world * point_steps * args.steps / (ms_max * 1e-3) / 1e9
-
-    # which kernel dominates and how long one launch takes (CUDA events on the ctx stream)
-    last = H.heat_last_run(ctx)
-    form_used = last["form"]
-    launches_per_run = max(1, last["launches"])
-    kernel_ms = statistics.mean(run_ms) / launches_per_run
+    # the dominant kernel: algorithmic work per launch over its average launch time
+    ki = runner.kernel_info(run_ms)
     pk = peaks()
-    steps_per_launch = nt / launches_per_run
-    units = float(n) * steps_per_launch          # point-steps per launch
     sms = torch.cuda.get_device_properties(local).multi_processor_count
-    kname = {("plain", "f64"): "k_plain_f64", ("plain", "f32c"): "k_plain_f32c", ("persist", "f64"): "k_persist",
-             ("persist", "f32c"): "k_persist", ("tblock", "f64"): "k_tblock", ("tblock", "f32c"): "k_tblock"}[
-        (form_used, w["dtype"])]
-    srcs = {"k_plain_f64": ["k_plain.cu"], "k_plain_f32c": ["k_plain.cu"], "k_persist": ["k_persist.cu"],
-            "k_tblock": ["k_tblock.cu"]}[kname]
-    srcs = [f"paper_2307_01117_gb300/csrc/{x}" for x in srcs] + ["paper_2307_01117_gb300/csrc/stencil_ops.cuh"]
-    # algorithmic HBM bytes: each point read once and written once per launch, whatever the steps per launch
-    # (one-step forms: 16 B per point-step in binary64; forms that keep T steps on chip: 16/T)
-    elem = 8.0 if w["dtype"] == "f64" else 4.0
-    alg_bytes = 2.0 * elem * float(n) * (steps_per_launch if form_used == "persist" else 1.0)
-    hbm_achieved = alg_bytes / (kernel_ms * 1e-3) / 1e9
-    roof_hbm = {"bound": "hbm", "achieved": hbm_achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                "frac": hbm_achieved / pk["hbm_gbs"], "peak_src": pk["src"], "alg_bytes_per_launch": alg_bytes}
+    launch_s = ki["launch_ms"] * 1e-3
+    hbm = ki["alg_bytes_per_launch"] / launch_s / 1e9
+    roof_hbm = {"bound": "hbm", "achieved": hbm, "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": hbm / pk["hbm_gbs"],
+                "peak_src": "measured (MEASURED_PEAKS.json hbm_gbs)" if pk["src"] == "measured" else "fallback",
+                "alg_bytes_per_launch": ki["alg_bytes_per_launch"]}
     if w["dtype"] == "f64":
-        dp_ops = DP_OPS[arith] * units
-        # DP pipe: 2 lane-operations per clock per SM (GB300 nominal 1.25 TFLOP/s FP64 with FMA = 2 flops)
+        ops = DP_OPS[args.arith] * ki["point_steps_per_launch"]
         dp_peak = 2.0 * sms * pk["sm_max_mhz"] * 1e6 / 1e9
-        achieved = dp_ops / (kernel_ms * 1e-3) / 1e9
+        achieved = ops / launch_s / 1e9
         roofline = {"bound": "alu", "achieved": achieved, "peak": dp_peak, "unit": "G DP-op/s",
                     "frac": achieved / dp_peak,
-                    "peak_src": f"2 DP ops/clk/SM x {sms} SMs x {pk['sm_max_mhz']:.0f} MHz (max SM clock)",
-                    "alg_ops_per_launch": dp_ops}
+                    "peak_src": f"FP64 unit: 2 ops/clk/SM x {sms} SMs x {pk['sm_max_mhz']:.0f} MHz max SM clock "
+                                f"(GB300 nominal 1.25 TFLOP/s FP64)",
+                    "alg_ops_per_launch": ops}
     else:
         roofline = dict(roof_hbm)
-    roofline["traffic"] = profile_traffic(kname, args.workload, srcs)
-    roofline["kernel"] = kname
-    roofline["launch_ms"] = kernel_ms
+    roofline["traffic"] = profile_traffic(ki["kernel"], args.workload, ki["src"])
+    roofline["kernel"] = ki["kernel"]
+    roofline["launch_ms"] = ki["launch_ms"]
+    roofline["launches_per_step"] = ki["launches"]
 
-    # end to end through the C ABI with host buffers: H2D of u0, run, sum, D2H of the state
     e2e = None
     if not args.no_e2e:
-        host_in = torch.empty(n, dtype=torch.float64, pin_memory=True).numpy()
-        host_in[:] = u0
-        host_out = torch.empty(n, dtype=torch.float64, pin_memory=True).numpy()
-        H.heat_set(ctx, host_in)
-        H.heat_run(ctx, nt)
-        H.heat_get(ctx, host_out)
+        runner.e2e_prepare()
+        runner.e2e_step()
         barrier()
         k_e2e = max(1, min(args.steps, 3))
         t0 = time.perf_counter()
         for _ in range(k_e2e):
-            H.heat_set(ctx, host_in)
-            H.heat_run(ctx, nt)
-            H.heat_sum(ctx)
-            H.heat_get(ctx, host_out)
+            runner.e2e_step()
         barrier()
-        dt_e2e = time.perf_counter() - t0
-        if dist is not None:
-            t = torch.tensor([dt_e2e], device=f"cuda:{local}")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            dt_e2e = float(t.item())
-        e2e = {"value": world * point_steps * k_e2e / dt_e2e / 1e9, "unit": UNIT, "h2d_bytes_per_step": n * 8,
-               "d2h_bytes_per_step": n * 8, "steps": k_e2e}
+        dt_e2e = max_over_ranks(time.perf_counter() - t0)
+        bi, bo = runner.e2e_bytes()
+        e2e = {"value": world * runner.point_steps * k_e2e / dt_e2e / 1e9, "unit": UNIT, "h2d_bytes_per_step": bi,
+               "d2h_bytes_per_step": bo, "steps": k_e2e}
 
     cb = None
-    if rank == 0 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cb = cpu_baseline(w)
 
-    launches = args.steps * (launches_per_run + 2)  # stencil launches + the two reduction kernels
+    launches = args.steps * (ki["launches"] + (2 if w["kind"] == "ring" else 0))
     if rank == 0:
+        cfg = runner.config()
+        cfg.update({"form": ki["form"], "T": ki["T"], "segments": ki["segments"],
+                    "parallelism": "replicas" if world > 1 else "single GPU"})
         line = {
-            "metric": METRIC if w["dtype"] == "f64" else METRIC_F32C, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "metric": METRIC[w["dtype"]], "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64" if w["dtype"] == "f64" else "f32", "data": "synthetic",
-            "config": {"workload": args.workload, "nx": w["nx"], "np": w["np"], "N": n, "nt": nt, "k": w["k"],
-                       "dt": w["dt"], "dx": w["dx"], "init": w["init"], "form": form_used, "T": last["T"],
-                       "segments": last["segments"] if form_used != "plain" else None,
-                       "arith": args.arith, "l2": "inputs larger than L2 (no flush needed)" if n * 8 > 2 * 135e6
-                       else "L2-resident ring", "parallelism": "replicas" if world > 1 else "single GPU"},
-            "roofline": roofline, "roofline_hbm": roof_hbm, "cpu_baseline": cb, "e2e": e2e,
+            "config": cfg, "roofline": roofline, "roofline_hbm": roof_hbm, "cpu_baseline": cb, "e2e": e2e,
             "gpu_launches": launches, "clocks": clk,
         }
         print(json.dumps(line), flush=True)
-    h.close()
+    runner.close()
     if dist is not None:
         dist.destroy_process_group()
     return 0

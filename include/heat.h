@@ -197,6 +197,91 @@ int heat_set_wait_limit(heat_ctx *c, int64_t ns);
  * disables the hook.  No GPU fault or trap is involved. */
 int heat_inject_stall(heat_ctx *c, int32_t segment, int64_t from_step);
 
+/* ---------------------------------------------------------------------------
+ * Batched rings: many independent instances of Section 2's problem, each with
+ * its own size, partition count, coefficient and step count, held in one
+ * device arena and advanced together by one persistent launch.  A ring's
+ * result is bitwise the one heat_run gives for it alone (binary64) or the one
+ * the temporal-blocking form gives with the same block depth (HEAT_F32C).
+ *
+ * The batch's kernel runs over a work table of units (level b, ring, segment):
+ * a ring of n points is cut into segments; level b advances a segment by T steps
+ * (fewer at the ring's last level); units are claimed in level order, and a unit
+ * waits (bounded) until its segment and the two neighbouring segments have
+ * finished level b-1.  T and the segment size come from heat_batch_set_tuning
+ * or heat_batch_autotune.
+ * ------------------------------------------------------------------------- */
+typedef struct heat_batch heat_batch; /* opaque, library-owned */
+
+/* Arena for `capacity_points` ring points (two buffers of that many elements of
+ * dtype, allocated now).  Each ring takes its n points rounded up to 64. */
+int heat_batch_create(heat_batch **out, int64_t capacity_points, heat_dtype dtype);
+
+/* Free the arena and tables (synchronises).  NULL is a no-op. */
+void heat_batch_destroy(heat_batch *b);
+
+/* Admit a ring of np x nx points with coefficient r = k*dt/dx^2 that will
+ * advance nt steps, initial state host_u (n = nx*np binary64 values, global
+ * order).  *ring_id receives its handle.  HEAT_ENOMEM when the arena has no
+ * contiguous room (the caller may wait for rings to be removed: admission by
+ * free device memory).  Synchronous copy. */
+int heat_batch_add(heat_batch *b, int64_t nx, int32_t np, double k, double dt, double dx, int64_t nt,
+                   const double *host_u, int32_t *ring_id);
+
+/* Same with the initial state in device memory (n binary64 values, 8-byte
+ * aligned); the copy is queued on the batch's stream (no wait). */
+int heat_batch_add_device(heat_batch *b, int64_t nx, int32_t np, double k, double dt, double dx, int64_t nt,
+                          const double *dev_u, int32_t *ring_id);
+
+/* Advance every ring that has steps left by min(steps left, max_steps) steps
+ * (max_steps <= 0: all remaining steps) in one persistent launch.
+ * Asynchronous on the batch's stream; device errors surface at heat_batch_sync
+ * or heat_batch_get. */
+int heat_batch_run(heat_batch *b, int64_t max_steps);
+
+/* Wait for the batch's stream; HEAT_ETIMEOUT if a dependency wait ran out. */
+int heat_batch_sync(heat_batch *b);
+
+/* Steps done and steps left of a ring. */
+int heat_batch_query(const heat_batch *b, int32_t ring_id, int64_t *steps_done, int64_t *steps_left);
+
+/* Copy a ring's current state to host memory (n binary64 values; synchronises). */
+int heat_batch_get(heat_batch *b, int32_t ring_id, double *host_u, int64_t n);
+
+/* Queue a copy of a ring's current state into device memory (n binary64
+ * values) on the batch's stream; no wait, no status check beyond a pending
+ * error seen at an earlier sync. */
+int heat_batch_get_device(heat_batch *b, int32_t ring_id, double *dev_u, int64_t n);
+
+/* Release a ring's arena space (its id becomes invalid). */
+int heat_batch_remove(heat_batch *b, int32_t ring_id);
+
+/* Temporal block depth T (1..64) and target segment length in points (>= 512);
+ * 0 keeps the current value (defaults: T = 4 for binary64, 16 for HEAT_F32C;
+ * segments of 16384 points). */
+int heat_batch_set_tuning(heat_batch *b, int T, int64_t seg_points);
+
+/* Pick T and the segment length by timing one level of the current rings for
+ * each candidate (the rings' states are not changed: one level only writes the
+ * idle buffer).  The choice is cached in the file named by the environment
+ * variable HEAT_TUNE_CACHE, if set, keyed by dtype and a coarse description of
+ * the batch.  Synchronous. */
+int heat_batch_autotune(heat_batch *b, int *T_out, int64_t *seg_points_out);
+
+/* Queue subsequent work on cuda_stream (NULL: the batch's own stream). */
+int heat_batch_set_stream(heat_batch *b, void *cuda_stream);
+
+/* Checkpoint of every live ring (its state and step count) into a device copy
+ * the batch keeps; heat_batch_restore puts those states back (and clears a
+ * pending device error).  Rings added after the save are left as they are. */
+int heat_batch_save(heat_batch *b);
+int heat_batch_restore(heat_batch *b);
+
+/* Live rings, free points in the arena (largest contiguous block), and the
+ * point-steps the last heat_batch_run queued. */
+int heat_batch_info(const heat_batch *b, int32_t *live_rings, int64_t *largest_free_points,
+                    int64_t *last_point_steps);
+
 /* Allocation-free stepper for callers that cannot allocate device memory
  * (inside CUDA graph capture, in real-time loops that must stay off the
  * allocator, or under another framework's memory pool).  The paper has no

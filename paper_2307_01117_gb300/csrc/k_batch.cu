@@ -1,0 +1,827 @@
+// k_batch.cu -- batched independent rings (the paper's Section 2 problem, many
+// instances at once) in one device arena, advanced by one persistent launch
+// driven by a work table.
+//
+// Work table (built on the host for each run, rings sorted by the number of
+// T-step levels they need, longest first):
+//   ring i: arena offset, n points, steps this run, nseg segments, r;
+//   units (level b, ring i, segment j) are numbered level-major, so the rings
+//   active at level b are a prefix of the sorted list and a unit number decodes
+//   with two binary searches (over the per-level and per-ring prefix sums).
+// A CTA claims the next unit from a launch-wide counter.  Unit (b, i, j) reads
+// the ring's state at time bT from one arena buffer and writes time
+// bT + steps_b into the other; before that it waits (bounded) until segments
+// j-1, j, j+1 of ring i have finished level b-1.  Because units are claimed in
+// level order and every CTA is co-resident (cooperative launch), the units it
+// waits for are already running, so the launch cannot deadlock.  That single
+// dependency also covers the write-after-read hazard on the output buffer,
+// which level b-1's neighbours read.
+//
+// Within a unit the CTA's warps cover the segment with register-resident
+// temporal-blocking windows (tb_core.cuh); windows wrap around the ring's ends
+// with modular indices.  Every point is computed from the same operands as in
+// the single-ring forms, so each ring's result is bitwise its solo result.
+#include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <map>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "tb_core.cuh"
+
+static constexpr int64_t kAlignPointsHost = 64;  // ring placement granularity in the arena (points)
+
+namespace heat {
+namespace {
+
+constexpr int kBWarps = 4;
+constexpr long long kMaxSpins = 1LL << 26;
+
+struct BRing {
+  int64_t off;        // arena offset in points
+  int64_t n;          // ring length
+  int64_t steps;      // steps this run
+  int64_t nseg;       // segments
+  int64_t done_base;  // index of segment 0's done counter
+  double r;
+  float rf;
+  int parity;         // arena buffer holding the state at the start of the run
+};
+
+struct BatchArgs {
+  void *arena0;
+  void *arena1;
+  const BRing *rings;
+  const int64_t *segp;    // prefix sums of nseg (count + 1)
+  const int64_t *levp;    // prefix sums of units per level (L + 1)
+  const int32_t *active;  // rings active at each level (L)
+  int L;
+  int T;
+  unsigned *done;
+  unsigned long long *counter;
+  DevStatus *st;
+  long long wait_ns;
+};
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void st_release_u32(unsigned *p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ unsigned long long now_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Bounded wait until *p >= target; false (and the device status set) if it ran out.
+__device__ bool wait_done(const BatchArgs &a, const unsigned *p, unsigned target, int ring, long long level) {
+  if (ld_acquire_u32(p) >= target) return true;
+  const unsigned long long deadline = now_ns() + (unsigned long long)a.wait_ns;
+  unsigned ns = 32;
+  for (long long spin = 0; spin < kMaxSpins; ++spin) {
+    if (ld_acquire_u32(p) >= target) return true;
+    if (*(volatile int *)&a.st->abort) return false;
+    if (now_ns() > deadline) break;
+    __nanosleep(ns);
+    if (ns < 1024) ns <<= 1;
+  }
+  if (atomicCAS(&a.st->code, HEAT_OK, HEAT_ETIMEOUT) == HEAT_OK) {
+    a.st->segment = ring;
+    a.st->step = level;
+  }
+  atomicExch(&a.st->abort, 1);
+  return false;
+}
+
+// Largest index k in [lo, hi) with v[k] <= x (v nondecreasing, v[lo] <= x).
+__device__ __forceinline__ int64_t floor_index(const int64_t *v, int64_t lo, int64_t hi, int64_t x) {
+  while (hi - lo > 1) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (v[mid] <= x) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(kBWarps * 32, MODE == 2 ? 4 : 6) k_batch(BatchArgs a) {
+  using P = tb::TB<MODE>;
+  using T = typename P::T;
+  constexpr int E = P::E;
+  constexpr int WIN = 32 * E;
+  __shared__ long long s_ring, s_level, s_lo, s_hi, s_steps, s_seg;
+  __shared__ int s_stop;
+  const int lane = threadIdx.x & 31;
+  const int wib = threadIdx.x >> 5;
+  const int64_t total = a.levp[a.L];
+  const int W = WIN - 2 * a.T;
+
+  for (;;) {
+    if (threadIdx.x == 0) {
+      const unsigned long long u = atomicAdd(a.counter, 1ull);
+      int stop = 0;
+      if ((int64_t)u >= total) {
+        stop = 1;
+      } else {
+        const int64_t b = floor_index(a.levp, 0, a.L, (int64_t)u);
+        const int64_t rel = (int64_t)u - a.levp[b];
+        const int64_t i = floor_index(a.segp, 0, a.active[b], rel);
+        const int64_t j = rel - a.segp[i];
+        const BRing R = a.rings[i];
+        if (b > 0) {
+          const int64_t jm = j == 0 ? R.nseg - 1 : j - 1, jp = j + 1 == R.nseg ? 0 : j + 1;
+          const unsigned tgt = (unsigned)b;
+          if (!(wait_done(a, a.done + R.done_base + jm, tgt, (int)i, b) &&
+                wait_done(a, a.done + R.done_base + j, tgt, (int)i, b) &&
+                wait_done(a, a.done + R.done_base + jp, tgt, (int)i, b)))
+            stop = 2;
+        }
+        s_ring = i;
+        s_level = b;
+        s_seg = j;
+        s_lo = (j * R.n) / R.nseg;
+        s_hi = ((j + 1) * R.n) / R.nseg;
+        const int64_t left = R.steps - b * a.T;
+        s_steps = left < a.T ? left : a.T;
+      }
+      s_stop = stop;
+    }
+    __syncthreads();
+    if (s_stop) break;  // uniform across the CTA
+    const BRing R = a.rings[s_ring];
+    const int par = R.parity ^ (int)(s_level & 1);
+    const T *src = (const T *)(par ? a.arena1 : a.arena0) + R.off;
+    T *dst = (T *)(par ? a.arena0 : a.arena1) + R.off;
+    const int64_t lo = s_lo, hi = s_hi, n = R.n;
+    const int steps = (int)s_steps;
+    const int64_t ntile = (hi - lo + W - 1) / W;
+    for (int64_t t = wib; t < ntile; t += kBWarps) {
+      const int64_t ws = lo + t * W - a.T;
+      typename P::Reg reg;
+      const bool inside = ws >= 0 && ws + WIN <= n;
+#pragma unroll
+      for (int k = 0; k < E; ++k) {
+        int64_t g = ws + 32 * k + lane;
+        if (!inside) {
+          g %= n;
+          if (g < 0) g += n;
+        }
+        P::load(reg, k, __ldcg(src + g));
+      }
+      for (int s = 0; s < steps; ++s) P::step(reg, lane, R.r, R.rf);
+      const int64_t out_hi = lo + (t + 1) * W < hi ? lo + (t + 1) * W : hi;
+#pragma unroll
+      for (int k = 0; k < E; ++k) {
+        const int i = 32 * k + lane;
+        const int64_t g = ws + i;
+        if (i >= a.T && g < out_hi) dst[g] = P::store(reg, k);
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();
+      st_release_u32(a.done + R.done_base + s_seg, (unsigned)(s_level + 1));
+    }
+  }
+}
+
+__global__ void k_b_f64_to_f32(const double *__restrict__ s, float *__restrict__ d, int64_t n) {
+  const int64_t st = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += st) d[i] = __double2float_rn(s[i]);
+}
+
+__global__ void k_b_f32_to_f64(const float *__restrict__ s, double *__restrict__ d, int64_t n) {
+  const int64_t st = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += st) d[i] = (double)s[i];
+}
+
+template <int MODE>
+int resident_ctas(int sms) {
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch<MODE>, kBWarps * 32, 0) != cudaSuccess)
+    return 0;
+  return per_sm * sms;
+}
+
+template <int MODE>
+cudaError_t launch_batch(BatchArgs &a, int grid, cudaStream_t st) {
+  void *params[] = {&a};
+  return cudaLaunchCooperativeKernel((const void *)k_batch<MODE>, dim3(grid), dim3(kBWarps * 32), params, 0, st);
+}
+
+}  // namespace
+}  // namespace heat
+
+using heat::BRing;
+
+struct heat_batch {
+  struct Ring {
+    bool live = false;
+    int64_t off = 0, len = 0, n = 0, nx = 0;
+    int32_t np = 0;
+    double r = 0;
+    float rf = 0;
+    int64_t nt = 0, done = 0;
+    int parity = 0;
+  };
+  heat_dtype dtype = HEAT_F64;
+  size_t elem = 8;
+  int device = 0, sms = 0;
+  void *arena[2] = {nullptr, nullptr};
+  int64_t capacity = 0;
+  std::map<int64_t, int64_t> free_blocks;  // offset -> length (points)
+  std::vector<Ring> rings;
+  std::vector<int32_t> free_ids;
+  cudaStream_t own_stream = nullptr, stream = nullptr;
+  heat::DevStatus *dstat = nullptr, *hstat = nullptr;
+  int host_error = HEAT_OK;
+  // device work table: one blob [rings | segp | levp | active], plus done counters
+  unsigned char *d_blob = nullptr;
+  size_t blob_cap = 0;
+  unsigned *d_done = nullptr;
+  size_t done_cap = 0;
+  unsigned long long *d_counter = nullptr;
+  // pinned staging for the blob, reused once `staged` has completed
+  unsigned char *h_stage = nullptr;
+  size_t stage_cap = 0;
+  cudaEvent_t staged = nullptr;
+  bool staged_pending = false;
+  int T = 0;
+  int64_t seg_points = 16384;
+  int64_t last_point_steps = 0;
+  long long wait_ns = 5000000000LL;
+  // saved states (heat_batch_save / heat_batch_restore)
+  void *snap = nullptr;
+  std::vector<std::pair<int64_t, int>> snap_state;  // per ring id: (done, live)
+};
+
+namespace {
+
+using heat::cuda_status;
+
+int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+
+int batch_sync_status(heat_batch *b) {
+  if (cudaStreamSynchronize(b->stream) != cudaSuccess) return HEAT_ECUDA;
+  if (cudaMemcpyAsync(b->hstat, b->dstat, sizeof(heat::DevStatus), cudaMemcpyDeviceToHost, b->stream) != cudaSuccess)
+    return HEAT_ECUDA;
+  if (cudaStreamSynchronize(b->stream) != cudaSuccess) return HEAT_ECUDA;
+  if (b->hstat->code != HEAT_OK && b->host_error == HEAT_OK) b->host_error = b->hstat->code;
+  return b->host_error;
+}
+
+// First-fit allocation of `len` points; -1 if no free block is large enough.
+int64_t arena_alloc(heat_batch *b, int64_t len) {
+  for (auto it = b->free_blocks.begin(); it != b->free_blocks.end(); ++it) {
+    if (it->second >= len) {
+      const int64_t off = it->first, rest = it->second - len;
+      b->free_blocks.erase(it);
+      if (rest > 0) b->free_blocks[off + len] = rest;
+      return off;
+    }
+  }
+  return -1;
+}
+
+void arena_free(heat_batch *b, int64_t off, int64_t len) {
+  auto it = b->free_blocks.emplace(off, len).first;
+  auto next = std::next(it);
+  if (next != b->free_blocks.end() && it->first + it->second == next->first) {
+    it->second += next->second;
+    b->free_blocks.erase(next);
+  }
+  if (it != b->free_blocks.begin()) {
+    auto prev = std::prev(it);
+    if (prev->first + prev->second == it->first) {
+      prev->second += it->second;
+      b->free_blocks.erase(it);
+    }
+  }
+}
+
+int default_T(const heat_batch *b) { return b->dtype == HEAT_F32C ? 16 : 4; }
+
+struct Table {
+  std::vector<BRing> rings;
+  std::vector<int32_t> ids;  // ring id of each table entry
+  std::vector<int64_t> segp, levp;
+  std::vector<int32_t> active;
+  int L = 0;
+  int64_t point_steps = 0;
+};
+
+// Work table for advancing each live ring by steps_of(ring) (> 0) steps.
+template <typename F>
+Table build_table(const heat_batch *b, int T, int64_t seg_points, F steps_of) {
+  Table t;
+  std::vector<std::pair<int64_t, int32_t>> order;  // (levels, id)
+  for (int32_t id = 0; id < (int32_t)b->rings.size(); ++id) {
+    const auto &r = b->rings[id];
+    if (!r.live) continue;
+    const int64_t s = steps_of(r);
+    if (s <= 0) continue;
+    order.push_back({(s + T - 1) / T, id});
+  }
+  std::stable_sort(order.begin(), order.end(),
+                   [](const std::pair<int64_t, int32_t> &x, const std::pair<int64_t, int32_t> &y) {
+                     return x.first > y.first;
+                   });
+  t.segp.push_back(0);
+  for (auto &o : order) {
+    const auto &r = b->rings[o.second];
+    BRing d;
+    d.off = r.off;
+    d.n = r.n;
+    d.steps = steps_of(r);
+    d.nseg = std::max<int64_t>(1, r.n / seg_points);
+    d.done_base = t.segp.back();
+    d.r = r.r;
+    d.rf = r.rf;
+    d.parity = r.parity;
+    t.rings.push_back(d);
+    t.ids.push_back(o.second);
+    t.segp.push_back(t.segp.back() + d.nseg);
+    t.point_steps += d.n * d.steps;
+  }
+  t.L = order.empty() ? 0 : (int)order.front().first;
+  t.levp.push_back(0);
+  size_t k = order.size();
+  for (int lev = 0; lev < t.L; ++lev) {
+    while (k > 0 && order[k - 1].first <= lev) --k;  // rings needing more than lev levels: order[0..k)
+    t.active.push_back((int32_t)k);
+    t.levp.push_back(t.levp.back() + t.segp[k]);
+  }
+  return t;
+}
+
+size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
+
+// Upload the table (one blob through pinned staging), zero the counters and
+// queue the persistent launch.
+int launch_table(heat_batch *b, const Table &t, int T) {
+  if (t.rings.empty()) return HEAT_OK;
+  const size_t nr = t.rings.size(), nl = (size_t)t.L;
+  const size_t o_rings = 0, o_segp = align16(o_rings + nr * sizeof(BRing));
+  const size_t o_levp = align16(o_segp + (nr + 1) * sizeof(int64_t));
+  const size_t o_act = align16(o_levp + (nl + 1) * sizeof(int64_t));
+  const size_t bytes = align16(o_act + nl * sizeof(int32_t));
+  // staging: wait for the previous upload to finish before reusing
+  if (b->staged_pending) {
+    if (cudaEventSynchronize(b->staged) != cudaSuccess) return HEAT_ECUDA;
+    b->staged_pending = false;
+  }
+  if (bytes > b->stage_cap) {
+    if (b->h_stage) cudaFreeHost(b->h_stage);
+    b->h_stage = nullptr;
+    b->stage_cap = 0;
+    if (cudaMallocHost((void **)&b->h_stage, bytes * 2) != cudaSuccess) return HEAT_ENOMEM;
+    b->stage_cap = bytes * 2;
+  }
+  if (bytes > b->blob_cap) {
+    if (b->d_blob) cudaFree(b->d_blob);
+    b->d_blob = nullptr;
+    b->blob_cap = 0;
+    if (cudaMalloc((void **)&b->d_blob, bytes * 2) != cudaSuccess) return HEAT_ENOMEM;
+    b->blob_cap = bytes * 2;
+  }
+  const size_t ndone = (size_t)t.segp.back();
+  if (ndone > b->done_cap) {
+    if (b->d_done) cudaFree(b->d_done);
+    b->d_done = nullptr;
+    b->done_cap = 0;
+    if (cudaMalloc((void **)&b->d_done, ndone * 2 * sizeof(unsigned)) != cudaSuccess) return HEAT_ENOMEM;
+    b->done_cap = ndone * 2;
+  }
+  memcpy(b->h_stage + o_rings, t.rings.data(), nr * sizeof(BRing));
+  memcpy(b->h_stage + o_segp, t.segp.data(), (nr + 1) * sizeof(int64_t));
+  memcpy(b->h_stage + o_levp, t.levp.data(), (nl + 1) * sizeof(int64_t));
+  memcpy(b->h_stage + o_act, t.active.data(), nl * sizeof(int32_t));
+  if (cudaMemcpyAsync(b->d_blob, b->h_stage, bytes, cudaMemcpyHostToDevice, b->stream) != cudaSuccess)
+    return HEAT_ECUDA;
+  if (cudaEventRecord(b->staged, b->stream) != cudaSuccess) return HEAT_ECUDA;
+  b->staged_pending = true;
+  if (cudaMemsetAsync(b->d_done, 0, ndone * sizeof(unsigned), b->stream) != cudaSuccess) return HEAT_ECUDA;
+  if (cudaMemsetAsync(b->d_counter, 0, sizeof(unsigned long long), b->stream) != cudaSuccess) return HEAT_ECUDA;
+
+  heat::BatchArgs a;
+  a.arena0 = b->arena[0];
+  a.arena1 = b->arena[1];
+  a.rings = (const BRing *)(b->d_blob + o_rings);
+  a.segp = (const int64_t *)(b->d_blob + o_segp);
+  a.levp = (const int64_t *)(b->d_blob + o_levp);
+  a.active = (const int32_t *)(b->d_blob + o_act);
+  a.L = t.L;
+  a.T = T;
+  a.done = b->d_done;
+  a.counter = b->d_counter;
+  a.st = b->dstat;
+  a.wait_ns = b->wait_ns;
+  const int64_t units = t.levp.back();
+  const bool f32 = b->dtype == HEAT_F32C;
+  const int resident = f32 ? heat::resident_ctas<2>(b->sms) : heat::resident_ctas<0>(b->sms);
+  if (resident < 1) return HEAT_ECUDA;
+  const int grid = (int)std::min<int64_t>(resident, units);
+  const cudaError_t e = f32 ? heat::launch_batch<2>(a, grid, b->stream) : heat::launch_batch<0>(a, grid, b->stream);
+  return e == cudaSuccess ? HEAT_OK : HEAT_ECUDA;
+}
+
+void free_batch(heat_batch *b) {
+  if (!b) return;
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  for (int i = 0; i < 2; ++i)
+    if (b->arena[i]) cudaFree(b->arena[i]);
+  if (b->dstat) cudaFree(b->dstat);
+  if (b->hstat) cudaFreeHost(b->hstat);
+  if (b->d_blob) cudaFree(b->d_blob);
+  if (b->d_done) cudaFree(b->d_done);
+  if (b->d_counter) cudaFree(b->d_counter);
+  if (b->h_stage) cudaFreeHost(b->h_stage);
+  if (b->staged) cudaEventDestroy(b->staged);
+  if (b->snap) cudaFree(b->snap);
+  if (b->own_stream) cudaStreamDestroy(b->own_stream);
+  delete b;
+}
+
+bool ring_ok(const heat_batch *b, int32_t id) { return id >= 0 && id < (int32_t)b->rings.size() && b->rings[id].live; }
+
+// Binary64 values (host or device) into the arena; binary32 state is rounded
+// on the device.
+int upload_ring(heat_batch *b, const heat_batch::Ring &r, const double *src_u, cudaMemcpyKind kind) {
+  void *dst = (char *)b->arena[r.parity] + (size_t)r.off * b->elem;
+  if (b->dtype == HEAT_F64)
+    return cudaMemcpyAsync(dst, src_u, (size_t)r.n * 8, kind, b->stream) == cudaSuccess ? HEAT_OK : HEAT_ECUDA;
+  if (kind == cudaMemcpyDeviceToDevice) {
+    const int grid = (int)std::min<int64_t>((r.n + 255) / 256, (int64_t)b->sms * 8);
+    heat::k_b_f64_to_f32<<<std::max(grid, 1), 256, 0, b->stream>>>(src_u, (float *)dst, r.n);
+    return cudaGetLastError() == cudaSuccess ? HEAT_OK : HEAT_ECUDA;
+  }
+  const double *host_u = src_u;
+  double *stage = nullptr;
+  if (cudaMalloc((void **)&stage, (size_t)r.n * 8) != cudaSuccess) return HEAT_ENOMEM;
+  int rc = HEAT_OK;
+  if (cudaMemcpyAsync(stage, host_u, (size_t)r.n * 8, cudaMemcpyHostToDevice, b->stream) != cudaSuccess) rc = HEAT_ECUDA;
+  if (rc == HEAT_OK) {
+    const int grid = (int)std::min<int64_t>((r.n + 255) / 256, (int64_t)b->sms * 8);
+    heat::k_b_f64_to_f32<<<std::max(grid, 1), 256, 0, b->stream>>>(stage, (float *)dst, r.n);
+    if (cudaGetLastError() != cudaSuccess) rc = HEAT_ECUDA;
+  }
+  if (cudaStreamSynchronize(b->stream) != cudaSuccess) rc = HEAT_ECUDA;
+  cudaFree(stage);
+  return rc;
+}
+
+}  // namespace
+
+extern "C" {
+
+int heat_batch_create(heat_batch **out, int64_t capacity_points, heat_dtype dtype) {
+  if (!out) return HEAT_EINVAL;
+  *out = nullptr;
+  if (capacity_points < 1 || (dtype != HEAT_F64 && dtype != HEAT_F32C)) return HEAT_EINVAL;
+  heat_batch *b = new (std::nothrow) heat_batch();
+  if (!b) return HEAT_ENOMEM;
+  b->dtype = dtype;
+  b->elem = dtype == HEAT_F64 ? 8 : 4;
+  b->capacity = round_up(capacity_points, kAlignPointsHost);
+  b->T = dtype == HEAT_F32C ? 16 : 4;
+  int rc = HEAT_OK;
+  if (cudaGetDevice(&b->device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, b->device) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&b->own_stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->staged, cudaEventDisableTiming) != cudaSuccess)
+    rc = HEAT_ECUDA;
+  b->stream = b->own_stream;
+  for (int i = 0; i < 2 && rc == HEAT_OK; ++i)
+    if (cudaMalloc(&b->arena[i], (size_t)b->capacity * b->elem) != cudaSuccess) rc = HEAT_ENOMEM;
+  if (rc == HEAT_OK && cudaMalloc((void **)&b->dstat, sizeof(heat::DevStatus)) != cudaSuccess) rc = HEAT_ENOMEM;
+  if (rc == HEAT_OK && cudaMallocHost((void **)&b->hstat, sizeof(heat::DevStatus)) != cudaSuccess) rc = HEAT_ENOMEM;
+  if (rc == HEAT_OK && cudaMalloc((void **)&b->d_counter, sizeof(unsigned long long)) != cudaSuccess) rc = HEAT_ENOMEM;
+  if (rc == HEAT_OK && cudaMemsetAsync(b->dstat, 0, sizeof(heat::DevStatus), b->stream) != cudaSuccess) rc = HEAT_ECUDA;
+  if (rc == HEAT_OK && cudaStreamSynchronize(b->stream) != cudaSuccess) rc = HEAT_ECUDA;
+  if (rc != HEAT_OK) {
+    cudaGetLastError();
+    free_batch(b);
+    return rc;
+  }
+  b->free_blocks[0] = b->capacity;
+  *out = b;
+  return HEAT_OK;
+}
+
+void heat_batch_destroy(heat_batch *b) { free_batch(b); }
+
+static int batch_add(heat_batch *b, int64_t nx, int32_t np, double k, double dt, double dx, int64_t nt,
+                     const double *src_u, cudaMemcpyKind kind, int32_t *ring_id) {
+  if (!b || !src_u || !ring_id || nx < 1 || np < 1 || nt < 0) return HEAT_EINVAL;
+  if (nx > INT64_MAX / np) return HEAT_EINVAL;
+  if (!isfinite(k) || !isfinite(dt) || !isfinite(dx) || dx == 0.0) return HEAT_EINVAL;
+  const double r = (k * dt) / (dx * dx);
+  if (!isfinite(r)) return HEAT_EINVAL;
+  heat_batch::Ring ring;
+  ring.n = nx * (int64_t)np;
+  ring.nx = nx;
+  ring.np = np;
+  ring.r = r;
+  ring.rf = (float)r;
+  ring.nt = nt;
+  ring.len = round_up(ring.n, kAlignPointsHost);
+  ring.off = arena_alloc(b, ring.len);
+  if (ring.off < 0) return HEAT_ENOMEM;
+  ring.live = true;
+  int32_t id;
+  if (!b->free_ids.empty()) {
+    id = b->free_ids.back();
+    b->free_ids.pop_back();
+    b->rings[id] = ring;
+  } else {
+    id = (int32_t)b->rings.size();
+    b->rings.push_back(ring);
+  }
+  int rc = upload_ring(b, b->rings[id], src_u, kind);
+  if (rc == HEAT_OK && kind == cudaMemcpyHostToDevice && cudaStreamSynchronize(b->stream) != cudaSuccess)
+    rc = HEAT_ECUDA;
+  if (rc != HEAT_OK) {
+    arena_free(b, ring.off, ring.len);
+    b->rings[id].live = false;
+    b->free_ids.push_back(id);
+    return rc;
+  }
+  *ring_id = id;
+  return HEAT_OK;
+}
+
+int heat_batch_add(heat_batch *b, int64_t nx, int32_t np, double k, double dt, double dx, int64_t nt,
+                   const double *host_u, int32_t *ring_id) {
+  return batch_add(b, nx, np, k, dt, dx, nt, host_u, cudaMemcpyHostToDevice, ring_id);
+}
+
+int heat_batch_add_device(heat_batch *b, int64_t nx, int32_t np, double k, double dt, double dx, int64_t nt,
+                          const double *dev_u, int32_t *ring_id) {
+  return batch_add(b, nx, np, k, dt, dx, nt, dev_u, cudaMemcpyDeviceToDevice, ring_id);
+}
+
+int heat_batch_run(heat_batch *b, int64_t max_steps) {
+  if (!b) return HEAT_EINVAL;
+  if (b->host_error != HEAT_OK) return HEAT_ESTATE;
+  const int T = b->T > 0 ? b->T : default_T(b);
+  Table t = build_table(b, T, b->seg_points, [&](const heat_batch::Ring &r) {
+    const int64_t left = r.nt - r.done;
+    return max_steps > 0 ? std::min(left, max_steps) : left;
+  });
+  b->last_point_steps = t.point_steps;
+  const int rc = launch_table(b, t, T);
+  if (rc != HEAT_OK) return rc;
+  for (size_t i = 0; i < t.rings.size(); ++i) {
+    auto &r = b->rings[t.ids[i]];
+    const int64_t levels = (t.rings[i].steps + T - 1) / T;
+    r.done += t.rings[i].steps;
+    r.parity ^= (int)(levels & 1);
+  }
+  return HEAT_OK;
+}
+
+int heat_batch_sync(heat_batch *b) {
+  if (!b) return HEAT_EINVAL;
+  return batch_sync_status(b);
+}
+
+int heat_batch_query(const heat_batch *b, int32_t ring_id, int64_t *steps_done, int64_t *steps_left) {
+  if (!b || !ring_ok(b, ring_id)) return HEAT_EINVAL;
+  const auto &r = b->rings[ring_id];
+  if (steps_done) *steps_done = r.done;
+  if (steps_left) *steps_left = r.nt - r.done;
+  return HEAT_OK;
+}
+
+int heat_batch_get(heat_batch *b, int32_t ring_id, double *host_u, int64_t n) {
+  if (!b || !host_u || !ring_ok(b, ring_id)) return HEAT_EINVAL;
+  const auto &r = b->rings[ring_id];
+  if (n != r.n) return HEAT_EINVAL;
+  int rc = batch_sync_status(b);
+  if (rc != HEAT_OK) return rc;
+  const void *src = (const char *)b->arena[r.parity] + (size_t)r.off * b->elem;
+  if (b->dtype == HEAT_F64) {
+    if (cudaMemcpyAsync(host_u, src, (size_t)n * 8, cudaMemcpyDeviceToHost, b->stream) != cudaSuccess)
+      return HEAT_ECUDA;
+  } else {
+    double *stage = nullptr;
+    if (cudaMalloc((void **)&stage, (size_t)n * 8) != cudaSuccess) return HEAT_ENOMEM;
+    const int grid = (int)std::min<int64_t>((n + 255) / 256, (int64_t)b->sms * 8);
+    heat::k_b_f32_to_f64<<<std::max(grid, 1), 256, 0, b->stream>>>((const float *)src, stage, n);
+    if (cudaGetLastError() != cudaSuccess ||
+        cudaMemcpyAsync(host_u, stage, (size_t)n * 8, cudaMemcpyDeviceToHost, b->stream) != cudaSuccess)
+      rc = HEAT_ECUDA;
+    cudaStreamSynchronize(b->stream);
+    cudaFree(stage);
+    if (rc != HEAT_OK) return rc;
+  }
+  return cudaStreamSynchronize(b->stream) == cudaSuccess ? HEAT_OK : HEAT_ECUDA;
+}
+
+int heat_batch_get_device(heat_batch *b, int32_t ring_id, double *dev_u, int64_t n) {
+  if (!b || !dev_u || !ring_ok(b, ring_id)) return HEAT_EINVAL;
+  const auto &r = b->rings[ring_id];
+  if (n != r.n) return HEAT_EINVAL;
+  if (b->host_error != HEAT_OK) return b->host_error;
+  const void *src = (const char *)b->arena[r.parity] + (size_t)r.off * b->elem;
+  if (b->dtype == HEAT_F64)
+    return cudaMemcpyAsync(dev_u, src, (size_t)n * 8, cudaMemcpyDeviceToDevice, b->stream) == cudaSuccess ? HEAT_OK
+                                                                                                       : HEAT_ECUDA;
+  const int grid = (int)std::min<int64_t>((n + 255) / 256, (int64_t)b->sms * 8);
+  heat::k_b_f32_to_f64<<<std::max(grid, 1), 256, 0, b->stream>>>((const float *)src, dev_u, n);
+  return cudaGetLastError() == cudaSuccess ? HEAT_OK : HEAT_ECUDA;
+}
+
+int heat_batch_remove(heat_batch *b, int32_t ring_id) {
+  if (!b || !ring_ok(b, ring_id)) return HEAT_EINVAL;
+  // queued work may still touch the ring's space
+  if (cudaStreamSynchronize(b->stream) != cudaSuccess) return HEAT_ECUDA;
+  auto &r = b->rings[ring_id];
+  arena_free(b, r.off, r.len);
+  r.live = false;
+  b->free_ids.push_back(ring_id);
+  return HEAT_OK;
+}
+
+int heat_batch_set_tuning(heat_batch *b, int T, int64_t seg_points) {
+  if (!b || T < 0 || T > heat::kMaxT || seg_points < 0 || (seg_points > 0 && seg_points < 512)) return HEAT_EINVAL;
+  const int win = b->dtype == HEAT_F32C ? 32 * heat::tb::TB<2>::E : 32 * heat::tb::TB<0>::E;
+  if (T > 0 && 2 * T >= win) return HEAT_EINVAL;
+  if (T > 0) b->T = T;
+  if (seg_points > 0) b->seg_points = seg_points;
+  return HEAT_OK;
+}
+
+int heat_batch_set_stream(heat_batch *b, void *cuda_stream) {
+  if (!b) return HEAT_EINVAL;
+  cudaStream_t next = cuda_stream ? (cudaStream_t)cuda_stream : b->own_stream;
+  if (next == b->stream) return HEAT_OK;
+  cudaEvent_t ev;
+  if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) return HEAT_ECUDA;
+  int rc = HEAT_OK;
+  if (cudaEventRecord(ev, b->stream) != cudaSuccess || cudaStreamWaitEvent(next, ev, 0) != cudaSuccess) rc = HEAT_ECUDA;
+  cudaEventDestroy(ev);
+  if (rc == HEAT_OK) b->stream = next;
+  return rc;
+}
+
+int heat_batch_info(const heat_batch *b, int32_t *live_rings, int64_t *largest_free_points,
+                    int64_t *last_point_steps) {
+  if (!b) return HEAT_EINVAL;
+  if (live_rings) {
+    int32_t c = 0;
+    for (const auto &r : b->rings) c += r.live ? 1 : 0;
+    *live_rings = c;
+  }
+  if (largest_free_points) {
+    int64_t m = 0;
+    for (const auto &f : b->free_blocks) m = std::max(m, f.second);
+    *largest_free_points = m;
+  }
+  if (last_point_steps) *last_point_steps = b->last_point_steps;
+  return HEAT_OK;
+}
+
+int heat_batch_save(heat_batch *b) {
+  if (!b) return HEAT_EINVAL;
+  int rc = batch_sync_status(b);
+  if (rc != HEAT_OK) return rc;
+  if (!b->snap && cudaMalloc(&b->snap, (size_t)b->capacity * b->elem) != cudaSuccess) return HEAT_ENOMEM;
+  b->snap_state.assign(b->rings.size(), {0, 0});
+  for (size_t id = 0; id < b->rings.size(); ++id) {
+    const auto &r = b->rings[id];
+    if (!r.live) continue;
+    const size_t o = (size_t)r.off * b->elem;
+    if (cudaMemcpyAsync((char *)b->snap + o, (const char *)b->arena[r.parity] + o, (size_t)r.n * b->elem,
+                        cudaMemcpyDeviceToDevice, b->stream) != cudaSuccess)
+      return HEAT_ECUDA;
+    b->snap_state[id] = {r.done, 1};
+  }
+  return cudaStreamSynchronize(b->stream) == cudaSuccess ? HEAT_OK : HEAT_ECUDA;
+}
+
+int heat_batch_restore(heat_batch *b) {
+  if (!b || !b->snap) return HEAT_ESTATE;
+  if (cudaStreamSynchronize(b->stream) != cudaSuccess) return HEAT_ECUDA;
+  for (size_t id = 0; id < b->rings.size() && id < b->snap_state.size(); ++id) {
+    auto &r = b->rings[id];
+    if (!r.live || !b->snap_state[id].second) continue;
+    const size_t o = (size_t)r.off * b->elem;
+    if (cudaMemcpyAsync((char *)b->arena[0] + o, (const char *)b->snap + o, (size_t)r.n * b->elem,
+                        cudaMemcpyDeviceToDevice, b->stream) != cudaSuccess)
+      return HEAT_ECUDA;
+    r.parity = 0;
+    r.done = b->snap_state[id].first;
+  }
+  b->host_error = HEAT_OK;
+  if (cudaMemsetAsync(b->dstat, 0, sizeof(heat::DevStatus), b->stream) != cudaSuccess) return HEAT_ECUDA;
+  return HEAT_OK;
+}
+
+int heat_batch_autotune(heat_batch *b, int *T_out, int64_t *seg_out) {
+  if (!b) return HEAT_EINVAL;
+  int rc = batch_sync_status(b);
+  if (rc != HEAT_OK) return rc;
+  // coarse description of the batch for the cache key
+  int64_t pts = 0, steps = 0;
+  int32_t live = 0;
+  for (const auto &r : b->rings)
+    if (r.live && r.nt > r.done) {
+      ++live;
+      pts += r.n;
+      steps += r.nt - r.done;
+    }
+  if (live == 0) return HEAT_ESTATE;
+  char key[160];
+  snprintf(key, sizeof(key), "batch dtype=%d rings_log2=%d points_log2=%d mean_n_log2=%d", (int)b->dtype,
+           (int)log2((double)live), (int)log2((double)pts), (int)log2((double)pts / live));
+  const char *cache = getenv("HEAT_TUNE_CACHE");
+  if (cache) {
+    FILE *f = fopen(cache, "r");
+    if (f) {
+      char line[256];
+      while (fgets(line, sizeof(line), f)) {
+        int T;
+        long long sg;
+        char k2[160];
+        // format: <key> | <T> <seg>
+        const char *bar = strchr(line, '|');
+        if (!bar) continue;
+        size_t kl = (size_t)(bar - line);
+        if (kl >= sizeof(k2)) continue;
+        memcpy(k2, line, kl);
+        while (kl > 0 && k2[kl - 1] == ' ') --kl;
+        k2[kl] = 0;
+        if (strcmp(k2, key) == 0 && sscanf(bar + 1, "%d %lld", &T, &sg) == 2) {
+          fclose(f);
+          b->T = T;
+          b->seg_points = sg;
+          if (T_out) *T_out = T;
+          if (seg_out) *seg_out = sg;
+          return HEAT_OK;
+        }
+      }
+      fclose(f);
+    }
+  }
+  const int Ts64[] = {2, 4, 8, 16};
+  const int Ts32[] = {8, 16, 32};
+  const int64_t segs[] = {4096, 16384, 65536};
+  const int *Ts = b->dtype == HEAT_F32C ? Ts32 : Ts64;
+  const int nT = b->dtype == HEAT_F32C ? 3 : 4;
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return HEAT_ECUDA;
+  double best = -1;
+  int bestT = b->T;
+  int64_t bestSeg = b->seg_points;
+  for (int ti = 0; ti < nT && rc == HEAT_OK; ++ti) {
+    for (int64_t sg : segs) {
+      const int T = Ts[ti];
+      // one level per ring: reads each ring's current buffer, writes only the idle one
+      Table t = build_table(b, T, sg, [&](const heat_batch::Ring &r) { return std::min<int64_t>(r.nt - r.done, T); });
+      for (int rep = 0; rep < 2 && rc == HEAT_OK; ++rep) {
+        cudaEventRecord(e0, b->stream);
+        rc = launch_table(b, t, T);
+        cudaEventRecord(e1, b->stream);
+        if (cudaEventSynchronize(e1) != cudaSuccess) rc = HEAT_ECUDA;
+      }
+      if (rc != HEAT_OK) break;
+      float ms = 0;
+      cudaEventElapsedTime(&ms, e0, e1);
+      const double rate = (double)t.point_steps / (ms * 1e-3);
+      if (rate > best) {
+        best = rate;
+        bestT = T;
+        bestSeg = sg;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc == HEAT_OK) rc = batch_sync_status(b);
+  if (rc != HEAT_OK) return rc;
+  b->T = bestT;
+  b->seg_points = bestSeg;
+  if (cache) {
+    FILE *f = fopen(cache, "a");
+    if (f) {
+      fprintf(f, "%s | %d %lld\n", key, bestT, (long long)bestSeg);
+      fclose(f);
+    }
+  }
+  if (T_out) *T_out = bestT;
+  if (seg_out) *seg_out = bestSeg;
+  return HEAT_OK;
+}
+
+}  // extern "C"

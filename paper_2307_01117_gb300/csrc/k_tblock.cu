@@ -29,167 +29,14 @@
 // per T steps in binary64, 8 B in binary32); the halo re-read adds WIN/W.
 #include <string.h>
 
-#include "dp_emul.cuh"
-#include "heat_internal.cuh"
-#include "stencil_ops.cuh"
+#include "tb_core.cuh"
 
 namespace heat {
 namespace {
 
-constexpr unsigned kFull = 0xffffffffu;
 constexpr int kWarps = 4;  // warps per CTA
 constexpr long long kMaxWaitSpins = 1LL << 24;
-
-__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(unsigned long long *bar, unsigned bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, unsigned parity) {
-  unsigned ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-__device__ __forceinline__ void bulk_load(void *sdst, const void *gsrc, unsigned bytes, unsigned long long *bar) {
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                   smem_u32(sdst)),
-               "l"(gsrc), "r"(bytes), "r"(smem_u32(bar))
-               : "memory");
-}
-
-__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-
-// ---- per-dtype register state and update --------------------------------------------
-template <int MODE>
-struct TB;
-
-template <int MODE>
-struct TBf64 {
-  using T = double;
-  static constexpr int E = 16;  // points per lane: window of 512
-  static constexpr int kAlign = 2;  // elements per 16 bytes
-  struct Reg {
-    double x[E];
-  };
-  static __device__ __forceinline__ void load(Reg &R, int k, double v) { R.x[k] = v; }
-  static __device__ __forceinline__ double store(const Reg &R, int k) { return R.x[k]; }
-  static __device__ __forceinline__ void step(Reg &R, int lane, double r, float) {
-    const int lm = (lane + 31) & 31, lp = (lane + 1) & 31;
-    double Lprev = __shfl_sync(kFull, R.x[0], lm);
-    double Rcur = __shfl_sync(kFull, R.x[0], lp);
-#pragma unroll
-    for (int k = 0; k < E; ++k) {
-      const double Lk = k == 0 ? Lprev : __shfl_sync(kFull, R.x[k], lm);
-      const double Rn = k + 1 < E ? __shfl_sync(kFull, R.x[k + 1], lp) : Rcur;
-      const double left = lane == 0 ? Lprev : Lk;
-      const double right = lane == 31 ? Rn : Rcur;
-      R.x[k] = eq2<MODE == 1>(left, R.x[k], right, r);
-      Lprev = Lk;
-      Rcur = Rn;
-    }
-  }
-  // The step with its multiply (and, for registers k whose bit is set in
-  // add_mask, its final add) done by the integer-pipe routines; the two
-  // differences stay on the FP64 unit.  Exact reading only.  The FP64 unit then
-  // issues 3 (or 2) operations per point instead of 4.
-  static __device__ __forceinline__ void step_split(Reg &R, int lane, const emul::Mul &m, unsigned add_mask,
-                                                    bool &bad) {
-    const int lm = (lane + 31) & 31, lp = (lane + 1) & 31;
-    double Lprev = __shfl_sync(kFull, R.x[0], lm);
-    double Rcur = __shfl_sync(kFull, R.x[0], lp);
-#pragma unroll
-    for (int k = 0; k < E; ++k) {
-      const double Lk = k == 0 ? Lprev : __shfl_sync(kFull, R.x[k], lm);
-      const double Rn = k + 1 < E ? __shfl_sync(kFull, R.x[k + 1], lp) : Rcur;
-      const double left = lane == 0 ? Lprev : Lk;
-      const double right = lane == 31 ? Rn : Rcur;
-      const double t1 = __fma_rn(-2.0, R.x[k], left);
-      const double t2 = __dadd_rn(t1, right);
-      const uint64_t t3 = emul::mul(m, (uint64_t)__double_as_longlong(t2), bad);
-      if ((add_mask >> k) & 1u)
-        R.x[k] = __longlong_as_double((long long)emul::add((uint64_t)__double_as_longlong(R.x[k]), t3, bad));
-      else
-        R.x[k] = __dadd_rn(R.x[k], __longlong_as_double((long long)t3));
-      Lprev = Lk;
-      Rcur = Rn;
-    }
-  }
-  // The same step with the integer-pipe binary64 routines (exact reading only).
-  static __device__ __forceinline__ void step_emul(Reg &R, int lane, const emul::Mul &m, bool &bad) {
-    const int lm = (lane + 31) & 31, lp = (lane + 1) & 31;
-    double Lprev = __shfl_sync(kFull, R.x[0], lm);
-    double Rcur = __shfl_sync(kFull, R.x[0], lp);
-#pragma unroll
-    for (int k = 0; k < E; ++k) {
-      const double Lk = k == 0 ? Lprev : __shfl_sync(kFull, R.x[k], lm);
-      const double Rn = k + 1 < E ? __shfl_sync(kFull, R.x[k + 1], lp) : Rcur;
-      const double left = lane == 0 ? Lprev : Lk;
-      const double right = lane == 31 ? Rn : Rcur;
-      const uint64_t v = emul::eq2_exact((uint64_t)__double_as_longlong(left), (uint64_t)__double_as_longlong(R.x[k]),
-                                         (uint64_t)__double_as_longlong(right), m, bad);
-      R.x[k] = __longlong_as_double((long long)v);
-      Lprev = Lk;
-      Rcur = Rn;
-    }
-  }
-};
-template <>
-struct TB<0> : TBf64<0> {};
-template <>
-struct TB<1> : TBf64<1> {};
-
-template <>
-struct TB<2> {
-  using T = float;
-  static constexpr int E = 32;  // window of 1024
-  static constexpr int kAlign = 4;
-  struct Reg {
-    float h[E];
-    float l[E];
-  };
-  static __device__ __forceinline__ void load(Reg &R, int k, float v) {
-    R.h[k] = v;
-    R.l[k] = 0.0f;
-  }
-  static __device__ __forceinline__ float store(const Reg &R, int k) { return f32c_store(R.h[k], R.l[k]); }
-  static __device__ __forceinline__ void step(Reg &R, int lane, double, float rf) {
-    const int lm = (lane + 31) & 31, lp = (lane + 1) & 31;
-    float Lh = __shfl_sync(kFull, R.h[0], lm), Ll = __shfl_sync(kFull, R.l[0], lm);
-    float Rh = __shfl_sync(kFull, R.h[0], lp), Rl = __shfl_sync(kFull, R.l[0], lp);
-#pragma unroll
-    for (int k = 0; k < E; ++k) {
-      const float Lkh = k == 0 ? Lh : __shfl_sync(kFull, R.h[k], lm);
-      const float Lkl = k == 0 ? Ll : __shfl_sync(kFull, R.l[k], lm);
-      const float Rnh = k + 1 < E ? __shfl_sync(kFull, R.h[k + 1], lp) : Rh;
-      const float Rnl = k + 1 < E ? __shfl_sync(kFull, R.l[k + 1], lp) : Rl;
-      const float lh = lane == 0 ? Lh : Lkh, ll = lane == 0 ? Ll : Lkl;
-      const float rh = lane == 31 ? Rnh : Rh, rl = lane == 31 ? Rnl : Rl;
-      float hn, ln;
-      eq2_f32c(lh, R.h[k], rh, ll, R.l[k], rl, rf, hn, ln);
-      R.h[k] = hn;
-      R.l[k] = ln;
-      Lh = Lkh;
-      Ll = Lkl;
-      Rh = Rnh;
-      Rl = Rnl;
-    }
-  }
-};
-
-template <int MODE>
-struct HasEmul {
-  static constexpr bool value = MODE == 0;
-};
+using namespace tb;
 
 struct TBArgs {
   const void *src;
@@ -384,7 +231,7 @@ int tblock_window(int dtype) { return dtype == HEAT_F32C ? 32 * TB<2>::E : 32 * 
 
 int run_tblock(heat_ctx *c, int64_t nt) {
   const int mode = c->dtype == HEAT_F32C ? 2 : (c->arith == HEAT_ARITH_FMA ? 1 : 0);
-  int T = c->T > 0 ? c->T : (c->dtype == HEAT_F32C ? 8 : 4);
+  int T = c->T > 0 ? c->T : (c->dtype == HEAT_F32C ? 16 : 4);
   const int WIN = tblock_window(c->dtype);
   if (2 * T >= WIN) return HEAT_EINVAL;
   c->last_T = T;

@@ -59,6 +59,22 @@ _PROTOS = {
     "heat_state_ptr": (_int, [_vp, ctypes.POINTER(_vp)]),
     "heat_set_wait_limit": (_int, [_vp, _i64]),
     "heat_inject_stall": (_int, [_vp, _i32, _i64]),
+    "heat_batch_create": (_int, [ctypes.POINTER(_vp), _i64, _int]),
+    "heat_batch_destroy": (None, [_vp]),
+    "heat_batch_add": (_int, [_vp, _i64, _i32, _d, _d, _d, _i64, _vp, ctypes.POINTER(_i32)]),
+    "heat_batch_add_device": (_int, [_vp, _i64, _i32, _d, _d, _d, _i64, _vp, ctypes.POINTER(_i32)]),
+    "heat_batch_get_device": (_int, [_vp, _i32, _vp, _i64]),
+    "heat_batch_run": (_int, [_vp, _i64]),
+    "heat_batch_sync": (_int, [_vp]),
+    "heat_batch_query": (_int, [_vp, _i32, ctypes.POINTER(_i64), ctypes.POINTER(_i64)]),
+    "heat_batch_get": (_int, [_vp, _i32, _vp, _i64]),
+    "heat_batch_remove": (_int, [_vp, _i32]),
+    "heat_batch_set_tuning": (_int, [_vp, _int, _i64]),
+    "heat_batch_autotune": (_int, [_vp, ctypes.POINTER(_int), ctypes.POINTER(_i64)]),
+    "heat_batch_set_stream": (_int, [_vp, _vp]),
+    "heat_batch_save": (_int, [_vp]),
+    "heat_batch_restore": (_int, [_vp]),
+    "heat_batch_info": (_int, [_vp, ctypes.POINTER(_i32), ctypes.POINTER(_i64), ctypes.POINTER(_i64)]),
     "heat_run_noalloc": (_int, [_vp, _vp, _i64, _d, _d, _d, _i64, _int, _vp]),
     "heat_strerror": (ctypes.c_char_p, [_int]),
 }
@@ -219,6 +235,91 @@ def heat_run_noalloc(dev_u0, dev_u, n: int, k: float, dt: float, dx: float, nt: 
     handle = None if stream is None else int(getattr(stream, "cuda_stream", stream))
     _check(lib().heat_run_noalloc(_dev_ptr(dev_u0), _dev_ptr(dev_u), int(n), float(k), float(dt), float(dx),
                                   int(nt), int(arith), handle), "heat_run_noalloc")
+
+
+def heat_batch_create(capacity_points: int, dtype: int = HEAT_F64) -> int:
+    h = _vp()
+    _check(lib().heat_batch_create(ctypes.byref(h), int(capacity_points), int(dtype)), "heat_batch_create")
+    return h.value
+
+
+def heat_batch_destroy(b: int) -> None:
+    lib().heat_batch_destroy(b)
+
+
+def heat_batch_add(b: int, nx: int, np_: int, k: float, dt: float, dx: float, nt: int, u) -> int:
+    a = np.ascontiguousarray(np.asarray(u, dtype=np.float64))
+    if a.size != int(nx) * int(np_):
+        raise ValueError("initial state must have nx*np values")
+    rid = _i32()
+    _check(lib().heat_batch_add(b, int(nx), int(np_), float(k), float(dt), float(dx), int(nt), a.ctypes.data,
+                                ctypes.byref(rid)), "heat_batch_add")
+    return rid.value
+
+
+def heat_batch_add_device(b: int, nx: int, np_: int, k: float, dt: float, dx: float, nt: int, dev_u) -> int:
+    rid = _i32()
+    _check(lib().heat_batch_add_device(b, int(nx), int(np_), float(k), float(dt), float(dx), int(nt),
+                                       _dev_ptr(dev_u), ctypes.byref(rid)), "heat_batch_add_device")
+    return rid.value
+
+
+def heat_batch_get_device(b: int, ring: int, dev_u, n: int) -> None:
+    _check(lib().heat_batch_get_device(b, int(ring), _dev_ptr(dev_u), int(n)), "heat_batch_get_device")
+
+
+def heat_batch_run(b: int, max_steps: int = 0) -> None:
+    _check(lib().heat_batch_run(b, int(max_steps)), "heat_batch_run")
+
+
+def heat_batch_sync(b: int) -> None:
+    _check(lib().heat_batch_sync(b), "heat_batch_sync")
+
+
+def heat_batch_query(b: int, ring: int) -> tuple[int, int]:
+    d, l = _i64(), _i64()
+    _check(lib().heat_batch_query(b, int(ring), ctypes.byref(d), ctypes.byref(l)), "heat_batch_query")
+    return d.value, l.value
+
+
+def heat_batch_get(b: int, ring: int, n: int, out: np.ndarray | None = None) -> np.ndarray:
+    if out is None:
+        out = np.empty(int(n), dtype=np.float64)
+    _check(lib().heat_batch_get(b, int(ring), out.ctypes.data, int(n)), "heat_batch_get")
+    return out
+
+
+def heat_batch_remove(b: int, ring: int) -> None:
+    _check(lib().heat_batch_remove(b, int(ring)), "heat_batch_remove")
+
+
+def heat_batch_set_tuning(b: int, T: int = 0, seg_points: int = 0) -> None:
+    _check(lib().heat_batch_set_tuning(b, int(T), int(seg_points)), "heat_batch_set_tuning")
+
+
+def heat_batch_autotune(b: int) -> tuple[int, int]:
+    T, sg = _int(), _i64()
+    _check(lib().heat_batch_autotune(b, ctypes.byref(T), ctypes.byref(sg)), "heat_batch_autotune")
+    return T.value, sg.value
+
+
+def heat_batch_set_stream(b: int, stream) -> None:
+    handle = None if stream is None else int(getattr(stream, "cuda_stream", stream))
+    _check(lib().heat_batch_set_stream(b, handle), "heat_batch_set_stream")
+
+
+def heat_batch_save(b: int) -> None:
+    _check(lib().heat_batch_save(b), "heat_batch_save")
+
+
+def heat_batch_restore(b: int) -> None:
+    _check(lib().heat_batch_restore(b), "heat_batch_restore")
+
+
+def heat_batch_info(b: int) -> dict:
+    live, free, ps = _i32(), _i64(), _i64()
+    _check(lib().heat_batch_info(b, ctypes.byref(live), ctypes.byref(free), ctypes.byref(ps)), "heat_batch_info")
+    return {"live": live.value, "largest_free": free.value, "last_point_steps": ps.value}
 
 
 class Heat:
