@@ -62,7 +62,16 @@ WORKLOADS = {
     "ring-2^28-f32c": dict(kind="ring", nx=1 << 20, np=256, nt=1000, k=0.25, dt=1.0, dx=1.0, init="modes1,7,64",
                            dtype="f32c"),
     "batch-4096-f64": dict(kind="batch", count=4096, seed=1, dtype="f64"),
+    # Poisson arrivals, N log-uniform in [1e4, 1e7], nt uniform in [100, 2000], r uniform in [0.05, 0.5],
+    # binary64 or binary32-compensated 50/50, 120 GB state budget; one step = one arrival window
+    "serve-2000": dict(kind="serve", rate=2000.0, duration=60.0, budget=120e9, seed=2, dtype="f64"),
+    "serve-100": dict(kind="serve", rate=100.0, duration=30.0, budget=120e9, seed=2, dtype="f64"),
     "batch-256-f64": dict(kind="batch", count=256, seed=1, dtype="f64"),
+    # binary32 compensated vs binary64 on np=256 x nx=2^20 (N = 2^28), nt = 10000, r = 0.25,
+    # u0 = sum of modes 1, 7, 64: timed binary32 runs, then errors against a binary64 run
+    # and the closed form sum_m lambda_m^nt sin(2 pi m g / N)
+    "precision-2^28": dict(kind="precision", nx=1 << 20, np=256, nt=10000, k=0.25, dt=1.0, dx=1.0,
+                           init="modes1,7,64", dtype="f32c", modes=(1, 7, 64)),
 }
 DEFAULT_WORKLOAD = "ring-2^28-f64"
 
@@ -369,6 +378,125 @@ class BatchRunner:
         self.H.heat_batch_destroy(self.b)
 
 
+class PrecisionRunner(RingRunner):
+    """Timed binary32-compensated runs; afterwards one binary64 run of the same ring
+    and the closed form give the error report."""
+
+    def accuracy(self):
+        torch, H, w = self.torch, self.H, self.w
+        n, nt = self.n, self.nt
+        # binary32 result of one run
+        self.step()
+        f32 = torch.empty(n, dtype=torch.float64, device=self.u0_dev.device)
+        H.heat_get_device(self.h.ctx, f32)
+        # binary64 result (exact reading, default form)
+        with H.Heat(w["nx"], w["np"], w["k"], w["dt"], w["dx"], dtype="f64", stream=self.stream) as h64:
+            H.heat_set_device(h64.ctx, self.u0_dev)
+            H.heat_run(h64.ctx, nt)
+            f64 = torch.empty_like(f32)
+            H.heat_get_device(h64.ctx, f64)
+            h64.sync()
+        torch.cuda.synchronize()
+        # closed form in binary64: sum_m lambda_m^nt sin(2 pi m g / N), phase reduced as (m g) mod N
+        r = w["k"] * w["dt"] / (w["dx"] * w["dx"])
+        g = torch.arange(n, dtype=torch.int64, device=f32.device)
+        exact = torch.zeros_like(f32)
+        for m in w["modes"]:
+            lam_n = float(np.exp(nt * np.log1p(-4.0 * r * np.sin(np.pi * m / n) ** 2)))
+            exact += lam_n * torch.sin((2.0 * np.pi / n) * ((m * g) % n).to(torch.float64))
+        del g
+        d = f32 - f64
+        rms = float(torch.sqrt(torch.mean(f64 * f64)))
+        amax = float(torch.max(torch.abs(f64)))
+        ulp32 = float(np.spacing(np.float32(amax)))
+        T = H.heat_last_run(self.h.ctx)["T"]
+        return {
+            "binary32_vs_binary64": {"max_abs": float(torch.max(torch.abs(d))),
+                                     "l2_rel": float(torch.sqrt(torch.mean(d * d))) / rms},
+            "binary64_vs_closed_form_max_abs": float(torch.max(torch.abs(f64 - exact))),
+            "binary32_vs_closed_form_max_abs": float(torch.max(torch.abs(f32 - exact))),
+            "initial_rounding_max_abs": float(torch.max(torch.abs(self.u0_dev - self.u0_dev.float().double()))),
+            "bound_binary32": (nt / T + 2) * ulp32, "bound_rule": "(nt/T + 2) ulp32(max|u|)", "T": T,
+            "max_abs_u": amax, "decay_mode64": float(np.exp(nt * np.log1p(-4.0 * r * np.sin(np.pi * 64 / n) ** 2))),
+        }
+
+
+class ServeRunner:
+    """One step = one window of Poisson arrivals replayed in real time through the
+    continuous-batching server (not drained at the window's end: unfinished
+    requests count as backlog)."""
+
+    def __init__(self, args, w, H, torch, local, stream):
+        from paper_2307_01117_gb300 import serve, workloads
+        self.args, self.w, self.H, self.torch, self.stream = args, w, H, torch, stream
+        self.serve, self.workloads = serve, workloads
+        self.rate = args.rate or w["rate"]
+        self.duration = args.duration or w["duration"]
+        self.windows = []
+        self.k = 0
+        self.point_steps = 0.0
+
+    def _window(self, duration, seed):
+        reqs = self.workloads.request_stream(rate=self.rate, duration=duration, seed=seed)
+        srv = self.serve.HeatServer(budget_bytes=self.w["budget"], tick_steps=self.args.tick, stream=self.stream)
+        try:
+            return srv.serve(reqs, duration=duration)
+        finally:
+            srv.close()
+
+    def step(self, ev=None):
+        if ev is None:   # warm-up: a short window
+            self._window(min(2.0, self.duration), self.w["seed"] + 1000 + self.k)
+            self.k += 1
+            return
+        ev[0].record(self.stream)
+        st = self._window(self.duration, self.w["seed"] + len(self.windows))
+        ev[1].record(self.stream)
+        self.windows.append(st)
+        self.point_steps = st.summary()["completed_point_steps"]
+
+    def e2e_prepare(self):
+        pass
+
+    def e2e_step(self):
+        pass
+
+    def e2e_bytes(self):
+        return 0, 0
+
+    def kernel_info(self, run_ms):
+        ticks = max(1, sum(st.ticks for st in self.windows))
+        ps = sum(st.gpu_point_steps for st in self.windows)
+        per_window = max(1, 2 * ticks // max(1, len(self.windows)))
+        return {"kernel": "k_batch", "src": ["paper_2307_01117_gb300/csrc/k_batch.cu",
+                                             "paper_2307_01117_gb300/csrc/tb_core.cuh"],
+                "launches": per_window, "launch_ms": statistics.mean(run_ms) / per_window,
+                "point_steps_per_launch": ps / (2 * ticks), "alg_bytes_per_launch": 0.0, "form": "serve",
+                "T": None, "segments": None}
+
+    def latency(self):
+        done = [d for st in self.windows for d in st.done]
+        lat = np.array([d.latency for d in done]) if done else np.zeros(0)
+        s = [st.summary() for st in self.windows]
+        return {"p50_s": float(np.percentile(lat, 50)) if lat.size else None,
+                "p99_s": float(np.percentile(lat, 99)) if lat.size else None,
+                "rate_req_s": self.rate, "window_s": self.duration,
+                "submitted": sum(x["submitted"] for x in s), "completed": sum(x["completed"] for x in s),
+                "backlog_at_window_end": sum(x["backlog"] for x in s),
+                "advanced_glups": statistics.mean(x["advanced_glups"] for x in s),
+                "max_inflight": max(x["max_inflight"] for x in s), "ticks": sum(x["ticks"] for x in s)}
+
+    def config(self):
+        return {"workload": self.args.workload, "rate_req_s": self.rate, "window_s": self.duration,
+                "budget_bytes": self.w["budget"], "tick_steps": self.args.tick,
+                "requests": "N log-uniform [1e4, 1e7], nt uniform [100, 2000], r uniform [0.05, 0.5], "
+                            "binary64 / binary32-compensated 50/50, u0 = U[-1,1) generated on the device",
+                "l2": "inputs larger than L2 (no flush needed)"}
+
+    def close(self):
+        pass
+
+
 # ---------------------------------------------------------------------------------------------
 
 def main() -> int:
@@ -385,6 +513,9 @@ def main() -> int:
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--rate", type=float, default=0.0, help="serving workloads: arrivals per second")
+    ap.add_argument("--duration", type=float, default=0.0, help="serving workloads: window length (s)")
+    ap.add_argument("--tick", type=int, default=256, help="serving workloads: steps per tick")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     w = dict(WORKLOADS[args.workload])
@@ -410,7 +541,8 @@ def main() -> int:
         hbuild.build()
 
     stream = torch.cuda.Stream()
-    runner = (RingRunner if w["kind"] == "ring" else BatchRunner)(args, w, H, torch, local, stream)
+    runner = {"ring": RingRunner, "batch": BatchRunner, "serve": ServeRunner,
+              "precision": PrecisionRunner}[w["kind"]](args, w, H, torch, local, stream)
 
     def barrier():
         torch.cuda.synchronize()
@@ -452,7 +584,10 @@ def main() -> int:
     roof_hbm = {"bound": "hbm", "achieved": hbm, "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": hbm / pk["hbm_gbs"],
                 "peak_src": "measured (MEASURED_PEAKS.json hbm_gbs)" if pk["src"] == "measured" else "fallback",
                 "alg_bytes_per_launch": ki["alg_bytes_per_launch"]}
-    if w["dtype"] == "f64":
+    if w["kind"] == "serve":
+        roofline = {"bound": "alu", "achieved": None, "peak": None, "unit": "G DP-op/s", "frac": None,
+                    "note": "mixed binary64 / binary32 requests; the ring and batch lines carry the kernel rooflines"}
+    elif w["dtype"] == "f64":
         ops = DP_OPS[args.arith] * ki["point_steps_per_launch"]
         dp_peak = 2.0 * sms * pk["sm_max_mhz"] * 1e6 / 1e9
         achieved = ops / launch_s / 1e9
@@ -469,7 +604,7 @@ def main() -> int:
     roofline["launches_per_step"] = ki["launches"]
 
     e2e = None
-    if not args.no_e2e:
+    if not args.no_e2e and w["kind"] != "serve":
         runner.e2e_prepare()
         runner.e2e_step()
         barrier()
@@ -484,10 +619,10 @@ def main() -> int:
                "d2h_bytes_per_step": bo, "steps": k_e2e}
 
     cb = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and w["kind"] != "serve":
         cb = cpu_baseline(w)
 
-    launches = args.steps * (ki["launches"] + (2 if w["kind"] == "ring" else 0))
+    launches = args.steps * (ki["launches"] + (2 if w["kind"] in ("ring", "precision") else 0))
     if rank == 0:
         cfg = runner.config()
         cfg.update({"form": ki["form"], "T": ki["T"], "segments": ki["segments"],
@@ -499,6 +634,11 @@ def main() -> int:
             "config": cfg, "roofline": roofline, "roofline_hbm": roof_hbm, "cpu_baseline": cb, "e2e": e2e,
             "gpu_launches": launches, "clocks": clk,
         }
+        if w["kind"] == "precision":
+            line["accuracy"] = runner.accuracy()
+        if w["kind"] == "serve":
+            line["latency"] = runner.latency()
+            line["metric"] = "serving: completed GLUP/s with p50/p99 request latency"
         print(json.dumps(line), flush=True)
     runner.close()
     if dist is not None:

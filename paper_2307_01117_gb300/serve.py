@@ -1,0 +1,193 @@
+"""Continuous-batching server for heat solves (Section 2's problem as requests).
+
+Requests (ring size, steps, coefficient, binary64 or binary32-compensated) are
+admitted into two device arenas (the batched-ring runtime, heat_batch_* in
+include/heat.h) as space frees up: admission is by free device memory under a
+byte budget, and a request's state stays resident on the device from admission
+to completion.  Every tick advances all admitted requests of each arena by up
+to `tick_steps` steps in one persistent launch per arena, so requests that
+arrive while others are running join the next tick and their work overlaps on
+the device.  A finished request's state is copied to host memory and its arena
+space released.
+
+Latency is measured from a request's arrival to the moment its result is on the
+host.  With `tick_steps` a multiple of the binary32 block depth T, each result
+is bitwise the one the request gets alone (binary64: heat_run; binary32: the
+temporal-blocking form with block depth T).
+"""
+from __future__ import annotations
+
+import collections
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import heat as H
+from .workloads import Request
+
+
+@dataclass
+class Done:
+    index: int
+    t_arrive: float
+    t_admit: float
+    t_done: float
+    n: int
+    nt: int
+    f32c: bool
+
+    @property
+    def latency(self) -> float:
+        return self.t_done - self.t_arrive
+
+
+@dataclass
+class ServeStats:
+    done: list = field(default_factory=list)
+    submitted: int = 0
+    rejected_too_large: int = 0
+    wall_s: float = 0.0
+    ticks: int = 0
+    max_inflight: int = 0
+    gpu_point_steps: float = 0.0
+
+    def summary(self) -> dict:
+        lat = np.array([d.latency for d in self.done]) if self.done else np.zeros(0)
+        ps = float(sum(d.n * d.nt for d in self.done))
+        return {
+            "submitted": self.submitted, "completed": len(self.done),
+            "backlog": self.submitted - len(self.done) - self.rejected_too_large,
+            "rejected_too_large": self.rejected_too_large,
+            "p50_s": float(np.percentile(lat, 50)) if lat.size else None,
+            "p99_s": float(np.percentile(lat, 99)) if lat.size else None,
+            "mean_s": float(lat.mean()) if lat.size else None,
+            "completed_point_steps": ps,
+            "completed_glups": ps / self.wall_s / 1e9 if self.wall_s > 0 else None,
+            "advanced_glups": self.gpu_point_steps / self.wall_s / 1e9 if self.wall_s > 0 else None,
+            "wall_s": self.wall_s, "ticks": self.ticks, "max_inflight": self.max_inflight,
+        }
+
+
+class HeatServer:
+    """budget_bytes: device memory for ring state (both arenas, both buffers)."""
+
+    def __init__(self, budget_bytes: float, tick_steps: int = 256, lookahead: int = 64, f32c_share: float = 1 / 3,
+                 T64: int = 0, T32: int = 16, stream=None, init_fn=None):
+        import torch
+        self.torch = torch
+        self.tick_steps = int(tick_steps)
+        self.lookahead = int(lookahead)
+        # binary64 points cost 16 bytes (two buffers), binary32 points 8 bytes
+        cap32 = max(1, int(budget_bytes * f32c_share) // 8)
+        cap64 = max(1, int(budget_bytes * (1 - f32c_share)) // 16)
+        self.caps = {False: cap64, True: cap32}
+        self.batch = {False: H.heat_batch_create(cap64, H.HEAT_F64), True: H.heat_batch_create(cap32, H.HEAT_F32C)}
+        self.stream = stream if stream is not None else torch.cuda.Stream()
+        for f32, b in self.batch.items():
+            H.heat_batch_set_stream(b, self.stream)
+        if T64:
+            H.heat_batch_set_tuning(self.batch[False], T64, 0)
+        H.heat_batch_set_tuning(self.batch[True], T32, 0)
+        if self.tick_steps % T32:
+            raise ValueError("tick_steps must be a multiple of the binary32 block depth")
+        self.init_fn = init_fn or self._device_uniform
+        self.queue: collections.deque = collections.deque()
+        self.inflight: dict = {}   # (f32c, ring id) -> (index, request, t_admit)
+        self.keep_alive: list = []  # device inputs whose copies are still queued
+        self.results: dict = {}    # index -> host array (when keep_results)
+
+    def _device_uniform(self, req: Request):
+        torch = self.torch
+        g = torch.Generator(device="cuda")
+        g.manual_seed(req.seed)
+        return torch.empty(req.n, dtype=torch.float64, device="cuda").uniform_(-1.0, 1.0, generator=g)
+
+    def close(self):
+        for b in self.batch.values():
+            H.heat_batch_destroy(b)
+        self.batch = {}
+
+    def submit(self, index: int, req: Request, stats: ServeStats) -> None:
+        stats.submitted += 1
+        if req.n + 64 > self.caps[req.f32c]:
+            stats.rejected_too_large += 1
+            return
+        self.queue.append((index, req))
+
+    def _admit(self, now: float) -> None:
+        kept = collections.deque()
+        looked = 0
+        while self.queue and looked < self.lookahead:
+            index, req = self.queue.popleft()
+            looked += 1
+            b = self.batch[req.f32c]
+            with self.torch.cuda.stream(self.stream):  # generate on the stream the copy is queued on
+                u = self.init_fn(req)
+            try:
+                rid = H.heat_batch_add_device(b, req.n, 1, req.r, 1.0, 1.0, req.nt, u)
+            except H.HeatError as e:
+                if e.code != H.HEAT_ENOMEM:
+                    raise
+                kept.append((index, req))   # no room yet: keep its place
+                continue
+            self.keep_alive.append(u)
+            self.inflight[(req.f32c, rid)] = (index, req, now)
+        kept.extend(self.queue)
+        self.queue = kept
+
+    def tick(self, t0: float, stats: ServeStats, keep_results: bool = False) -> int:
+        """Admit, advance every admitted request by up to tick_steps, collect the
+        finished ones.  Returns the number of requests still in flight."""
+        self._admit(time.perf_counter() - t0)
+        if not self.inflight:
+            return 0
+        stats.max_inflight = max(stats.max_inflight, len(self.inflight))
+        for f32, b in self.batch.items():
+            H.heat_batch_run(b, self.tick_steps)
+            stats.gpu_point_steps += H.heat_batch_info(b)["last_point_steps"]
+        for b in self.batch.values():
+            H.heat_batch_sync(b)
+        self.keep_alive.clear()
+        stats.ticks += 1
+        finished = []
+        for key, (index, req, t_admit) in self.inflight.items():
+            f32, rid = key
+            if H.heat_batch_query(self.batch[f32], rid)[1] == 0:
+                finished.append(key)
+        for key in finished:
+            f32, rid = key
+            index, req, t_admit = self.inflight.pop(key)
+            out = H.heat_batch_get(self.batch[f32], rid, req.n)
+            H.heat_batch_remove(self.batch[f32], rid)
+            stats.done.append(Done(index, req.t_arrive, t_admit, time.perf_counter() - t0, req.n, req.nt, f32))
+            if keep_results:
+                self.results[index] = out
+        return len(self.inflight)
+
+    def serve(self, requests: list[Request], duration: float | None = None, drain: bool = False,
+              keep_results: bool = False) -> ServeStats:
+        """Replay `requests` (arrival times in seconds from the start) in real time.
+        Stops at `duration` (default: the last arrival) unless drain is set, in
+        which case it runs until every admitted or queued request is done."""
+        stats = ServeStats()
+        reqs = sorted(enumerate(requests), key=lambda x: x[1].t_arrive)
+        horizon = duration if duration is not None else (reqs[-1][1].t_arrive if reqs else 0.0)
+        t0 = time.perf_counter()
+        nxt = 0
+        while True:
+            now = time.perf_counter() - t0
+            while nxt < len(reqs) and reqs[nxt][1].t_arrive <= now and reqs[nxt][1].t_arrive <= horizon:
+                self.submit(reqs[nxt][0], reqs[nxt][1], stats)
+                nxt += 1
+            arrivals_left = nxt < len(reqs) and reqs[nxt][1].t_arrive <= horizon
+            if now >= horizon and not drain:
+                break
+            if not self.queue and not self.inflight:
+                if not arrivals_left:
+                    break
+                time.sleep(max(0.0, min(0.01, reqs[nxt][1].t_arrive - now)))
+                continue
+            self.tick(t0, stats, keep_results)
+        stats.wall_s = time.perf_counter() - t0
+        return stats
