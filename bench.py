@@ -67,6 +67,8 @@ WORKLOADS = {
     "serve-2000": dict(kind="serve", rate=2000.0, duration=60.0, budget=120e9, seed=2, dtype="f64"),
     "serve-100": dict(kind="serve", rate=100.0, duration=30.0, budget=120e9, seed=2, dtype="f64"),
     "batch-256-f64": dict(kind="batch", count=256, seed=1, dtype="f64"),
+    # profiling case: 256 rings of the same size law, nt uniform in [100, 300]
+    "batch-prof-f64": dict(kind="batch", count=256, seed=1, dtype="f64", nt_lo=100, nt_hi=300),
     # binary32 compensated vs binary64 on np=256 x nx=2^20 (N = 2^28), nt = 10000, r = 0.25,
     # u0 = sum of modes 1, 7, 64: timed binary32 runs, then errors against a binary64 run
     # and the closed form sum_m lambda_m^nt sin(2 pi m g / N)
@@ -186,7 +188,7 @@ def cpu_baseline(w: dict, seconds: float = 12.0) -> dict:
     import oracle
     if w["kind"] == "batch":
         from paper_2307_01117_gb300 import workloads
-        specs = workloads.ring_table(w["count"], seed=w["seed"])
+        specs = workloads.ring_table(w["count"], seed=w["seed"], nt_lo=w.get("nt_lo", 100), nt_hi=w.get("nt_hi", 5000))
         done_pts, total, rings = 0, 0.0, 0
         for spec in specs:
             if total >= seconds:
@@ -311,7 +313,8 @@ class BatchRunner:
     def __init__(self, args, w, H, torch, local, stream):
         from paper_2307_01117_gb300 import workloads
         self.args, self.w, self.H, self.torch, self.stream = args, w, H, torch, stream
-        self.specs = workloads.ring_table(w["count"], seed=w["seed"])
+        self.specs = workloads.ring_table(w["count"], seed=w["seed"], nt_lo=w.get("nt_lo", 100),
+                                          nt_hi=w.get("nt_hi", 5000))
         self.inits = [workloads.ring_initial(s) for s in self.specs]
         self.n_total = sum(s.n for s in self.specs)
         self.point_steps = float(sum(s.n * s.nt for s in self.specs))
@@ -597,7 +600,15 @@ def main() -> int:
                                 f"(GB300 nominal 1.25 TFLOP/s FP64)",
                     "alg_ops_per_launch": ops}
     else:
-        roofline = dict(roof_hbm)
+        # binary32 compensated: 13 FP32 operations per point-step (two fused differences
+        # and their adds, the sum, the product, TwoSum's six, the correction add)
+        ops = 13.0 * ki["point_steps_per_launch"]
+        fp32_peak = 128.0 * sms * pk["sm_max_mhz"] * 1e6 / 1e12
+        achieved = ops / launch_s / 1e12
+        roofline = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "T FP32-op/s",
+                    "frac": achieved / fp32_peak,
+                    "peak_src": f"FP32 pipe: 128 ops/clk/SM x {sms} SMs x {pk['sm_max_mhz']:.0f} MHz max SM clock",
+                    "alg_ops_per_launch": ops}
     roofline["traffic"] = profile_traffic(ki["kernel"], args.workload, ki["src"])
     roofline["kernel"] = ki["kernel"]
     roofline["launch_ms"] = ki["launch_ms"]

@@ -69,8 +69,16 @@ typedef enum {
   HEAT_FORM_PERSIST = 1, /* one persistent launch; each CTA owns a segment and
                             swaps ghost values with its neighbours through
                             device-memory flag queues (Section 2's SPSC queues) */
-  HEAT_FORM_TBLOCK = 2,  /* temporal blocking: T steps per shared-memory tile */
-  HEAT_FORM_AUTO = 3     /* library picks by ring size and dtype */
+  HEAT_FORM_TBLOCK = 2,  /* temporal blocking: T steps per register-resident tile */
+  HEAT_FORM_AUTO = 3,    /* library picks: HEAT_FORM_CLUSTER for small rings,
+                            HEAT_FORM_TBLOCK otherwise */
+  HEAT_FORM_CLUSTER = 4  /* small rings (up to 16 x 4 windows of output, about
+                            31000 binary64 points at T = 8): one thread-block
+                            cluster of up to 16 CTAs runs all nt steps in one
+                            launch; each CTA keeps its segment in shared memory
+                            and reads its neighbours' T-point halos through
+                            distributed shared memory, one cluster barrier per
+                            block of T steps */
 } heat_form;
 
 /* Rounding reading of Eq. 2 for HEAT_F64 (the paper states no order). */
@@ -129,7 +137,9 @@ int heat_sync(heat_ctx *c);
 int heat_set_stream(heat_ctx *c, void *cuda_stream);
 
 /* Select the kernel form and, for HEAT_FORM_TBLOCK, the temporal block depth
- * T (1..64; 0 = library default).  T is ignored by the other forms. */
+ * T (1..64; 0 = library default: 4 for HEAT_F64, 32 for HEAT_F32C).  T is
+ * ignored by the other forms.  HEAT_FORM_AUTO (the default) is
+ * HEAT_FORM_TBLOCK. */
 int heat_set_form(heat_ctx *c, int form, int T);
 
 /* Segmentation of the persistent forms: 0 = library default (near-equal
@@ -158,6 +168,13 @@ int heat_set_emulation(heat_ctx *c, int share);
  * there).  Bitwise the same state for every level (every operation is the
  * correctly rounded IEEE result either way). */
 int heat_set_split(heat_ctx *c, int level);
+
+/* Register layout of the temporal-blocking form: 0 = strided (lane l holds
+ * window points 32k + l; windows staged into shared memory by bulk TMA copies),
+ * 1 = contiguous (lane l holds E consecutive points; neighbours inside a lane
+ * come from its own registers, so a step needs two shuffles per lane instead of
+ * two per point; the default).  The state is bitwise the same for either layout. */
+int heat_set_layout(heat_ctx *c, int layout);
 
 /* Select the rounding reading for HEAT_F64 (heat_arith).  HEAT_F32C ignores it. */
 int heat_set_arith(heat_ctx *c, int arith);
@@ -257,7 +274,7 @@ int heat_batch_get_device(heat_batch *b, int32_t ring_id, double *dev_u, int64_t
 int heat_batch_remove(heat_batch *b, int32_t ring_id);
 
 /* Temporal block depth T (1..64) and target segment length in points (>= 512);
- * 0 keeps the current value (defaults: T = 4 for binary64, 16 for HEAT_F32C;
+ * 0 keeps the current value (defaults: T = 4 for binary64, 32 for HEAT_F32C;
  * segments of 16384 points). */
 int heat_batch_set_tuning(heat_batch *b, int T, int64_t seg_points);
 
@@ -270,6 +287,12 @@ int heat_batch_autotune(heat_batch *b, int *T_out, int64_t *seg_points_out);
 
 /* Queue subsequent work on cuda_stream (NULL: the batch's own stream). */
 int heat_batch_set_stream(heat_batch *b, void *cuda_stream);
+
+/* Cap the batch kernel's CTAs per SM (0: as many as fit).  The launch needs no
+ * co-residency, so two batches on two streams with caps that together fit an
+ * SM run side by side: a binary64 batch (FP64 unit) and a binary32 batch
+ * (FP32 and integer pipes) then share every SM. */
+int heat_batch_set_ctas_per_sm(heat_batch *b, int ctas_per_sm);
 
 /* Checkpoint of every live ring (its state and step count) into a device copy
  * the batch keeps; heat_batch_restore puts those states back (and clears a

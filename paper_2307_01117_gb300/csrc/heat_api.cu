@@ -13,6 +13,7 @@ namespace {
 constexpr int64_t kStageElems = int64_t(1) << 22;  // binary64 staging chunk for HEAT_F32C transfers (32 MiB)
 constexpr int kDefaultEmulShare = 0;               // tiles of 32 on the integer pipes by default
 constexpr int kDefaultSplit = 0;                   // per-point FP64/integer split level by default
+constexpr int64_t kClusterAutoPoints = 8192;       // rings up to this size use the cluster form by default
 
 bool is_finite(double x) { return isfinite(x) != 0; }
 
@@ -83,6 +84,7 @@ int heat_create(heat_ctx **out, int64_t nx, int32_t np, double k, double dt, dou
   c->inj_step = 0;
   heat_set_emulation(c, kDefaultEmulShare);
   heat_set_split(c, kDefaultSplit);
+  c->tb_layout = 1;  // contiguous per-lane ownership (measured fastest for both dtypes)
   int rc = HEAT_OK;
   if (cudaGetDevice(&c->device) != cudaSuccess ||
       cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess) {
@@ -202,9 +204,11 @@ int heat_run(heat_ctx *c, int64_t nt) {
   if (c->host_error != HEAT_OK) return HEAT_ESTATE;
   if (nt == 0) return HEAT_OK;
   int form = c->form;
-  // default: temporal blocking (the fastest form measured for both dtypes on
-  // large rings; on small rings it also needs T times fewer launches)
-  if (form == HEAT_FORM_AUTO) form = HEAT_FORM_TBLOCK;
+  // default: one cluster launch for small rings (latency-bound: one launch for
+  // all steps, ghost exchange through distributed shared memory), temporal
+  // blocking otherwise (the fastest form measured for both dtypes)
+  if (form == HEAT_FORM_AUTO)
+    form = c->geo.N <= kClusterAutoPoints ? HEAT_FORM_CLUSTER : HEAT_FORM_TBLOCK;
   c->last_form = form;
   c->last_T = 1;
   c->last_launches = 0;
@@ -212,6 +216,7 @@ int heat_run(heat_ctx *c, int64_t nt) {
     case HEAT_FORM_PLAIN: return heat::run_plain(c, nt);
     case HEAT_FORM_PERSIST: return heat::run_persist(c, nt);
     case HEAT_FORM_TBLOCK: return heat::run_tblock(c, nt);
+    case HEAT_FORM_CLUSTER: return heat::run_cluster(c, nt);
     default: return HEAT_EINVAL;
   }
 }
@@ -246,10 +251,16 @@ int heat_set_stream(heat_ctx *c, void *cuda_stream) {
 
 int heat_set_form(heat_ctx *c, int form, int T) {
   if (!c) return HEAT_EINVAL;
-  if (form < HEAT_FORM_PLAIN || form > HEAT_FORM_AUTO) return HEAT_EINVAL;
+  if (form < HEAT_FORM_PLAIN || form > HEAT_FORM_CLUSTER) return HEAT_EINVAL;
   if (T < 0 || T > heat::kMaxT) return HEAT_EINVAL;
   c->form = form;
   c->T = T;
+  return HEAT_OK;
+}
+
+int heat_set_layout(heat_ctx *c, int layout) {
+  if (!c || layout < 0 || layout > 1) return HEAT_EINVAL;
+  c->tb_layout = layout;
   return HEAT_OK;
 }
 

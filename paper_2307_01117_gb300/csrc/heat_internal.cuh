@@ -72,6 +72,7 @@ struct heat_ctx {
   int emul_share;                // tiles of 32 computed on the integer pipes (binary64, exact reading)
   unsigned emul_mask;            // the same as a bit mask over tile index mod 32
   int split_level;               // per-point split of the binary64 update between FP64 unit and integer pipes
+  int tb_layout;                 // temporal-blocking register layout: 0 strided (TMA-staged), 1 contiguous
   double *partials;              // reduction scratch, device
   unsigned long long *tile_counter;  // dynamic tile counter of the temporal-blocking form, device
   double *hsum;                  // pinned host word for heat_sum
@@ -86,6 +87,8 @@ namespace heat {
 int run_plain(heat_ctx *c, int64_t nt);
 int run_persist(heat_ctx *c, int64_t nt);
 int run_tblock(heat_ctx *c, int64_t nt);
+int run_cluster(heat_ctx *c, int64_t nt);
+int64_t cluster_max_points(const heat_ctx *c, int T);
 int sum_state(heat_ctx *c, double *out);
 int convert_f64_to_state(heat_ctx *c, const double *dev_src, void *dev_dst, int64_t n);
 int convert_state_to_f64(heat_ctx *c, const void *dev_src, double *dev_dst, int64_t n);

@@ -11,11 +11,15 @@
 // A CTA claims the next unit from a launch-wide counter.  Unit (b, i, j) reads
 // the ring's state at time bT from one arena buffer and writes time
 // bT + steps_b into the other; before that it waits (bounded) until segments
-// j-1, j, j+1 of ring i have finished level b-1.  Because units are claimed in
-// level order and every CTA is co-resident (cooperative launch), the units it
-// waits for are already running, so the launch cannot deadlock.  That single
-// dependency also covers the write-after-read hazard on the output buffer,
-// which level b-1's neighbours read.
+// j-1, j, j+1 of ring i have finished level b-1.  Units are numbered level-major
+// and claimed in increasing order, so every unit a CTA waits for has a smaller
+// number and was claimed earlier by a CTA that is running it; the CTA holding
+// the smallest unfinished unit therefore never waits on anything unfinished,
+// and the launch makes progress with any number of resident CTAs.  No
+// co-residency is needed: the kernel is an ordinary launch, and two batches
+// (binary64 and binary32) can share the GPU.  The same wait covers the
+// write-after-read hazard on the output buffer, which level b-1's neighbours
+// read.
 //
 // Within a unit the CTA's warps cover the segment with register-resident
 // temporal-blocking windows (tb_core.cuh); windows wrap around the ring's ends
@@ -114,8 +118,8 @@ __device__ __forceinline__ int64_t floor_index(const int64_t *v, int64_t lo, int
 }
 
 template <int MODE>
-__global__ void __launch_bounds__(kBWarps * 32, MODE == 2 ? 4 : 6) k_batch(BatchArgs a) {
-  using P = tb::TB<MODE>;
+__global__ void __launch_bounds__(kBWarps * 32, MODE == 2 ? 3 : 5) k_batch(BatchArgs a) {
+  using P = tb::TBC<MODE>;  // contiguous per-lane ownership
   using T = typename P::T;
   constexpr int E = P::E;
   constexpr int WIN = 32 * E;
@@ -171,7 +175,7 @@ __global__ void __launch_bounds__(kBWarps * 32, MODE == 2 ? 4 : 6) k_batch(Batch
       const bool inside = ws >= 0 && ws + WIN <= n;
 #pragma unroll
       for (int k = 0; k < E; ++k) {
-        int64_t g = ws + 32 * k + lane;
+        int64_t g = ws + E * lane + k;
         if (!inside) {
           g %= n;
           if (g < 0) g += n;
@@ -182,9 +186,9 @@ __global__ void __launch_bounds__(kBWarps * 32, MODE == 2 ? 4 : 6) k_batch(Batch
       const int64_t out_hi = lo + (t + 1) * W < hi ? lo + (t + 1) * W : hi;
 #pragma unroll
       for (int k = 0; k < E; ++k) {
-        const int i = 32 * k + lane;
+        const int i = E * lane + k;
         const int64_t g = ws + i;
-        if (i >= a.T && g < out_hi) dst[g] = P::store(reg, k);
+        if (i >= a.T && i < WIN - a.T && g < out_hi) dst[g] = P::store(reg, k);
       }
     }
     __syncthreads();
@@ -206,17 +210,16 @@ __global__ void k_b_f32_to_f64(const float *__restrict__ s, double *__restrict__
 }
 
 template <int MODE>
-int resident_ctas(int sms) {
-  int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch<MODE>, kBWarps * 32, 0) != cudaSuccess)
-    return 0;
-  return per_sm * sms;
+cudaError_t launch_batch(BatchArgs &a, int grid, cudaStream_t st) {
+  k_batch<MODE><<<grid, kBWarps * 32, 0, st>>>(a);
+  return cudaGetLastError();
 }
 
 template <int MODE>
-cudaError_t launch_batch(BatchArgs &a, int grid, cudaStream_t st) {
-  void *params[] = {&a};
-  return cudaLaunchCooperativeKernel((const void *)k_batch<MODE>, dim3(grid), dim3(kBWarps * 32), params, 0, st);
+int per_sm_ctas() {
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch<MODE>, kBWarps * 32, 0) != cudaSuccess) return 0;
+  return per_sm;
 }
 
 }  // namespace
@@ -257,6 +260,7 @@ struct heat_batch {
   cudaEvent_t staged = nullptr;
   bool staged_pending = false;
   int T = 0;
+  int ctas_per_sm = 0;  // 0: as many as fit
   int64_t seg_points = 16384;
   int64_t last_point_steps = 0;
   long long wait_ns = 5000000000LL;
@@ -309,7 +313,7 @@ void arena_free(heat_batch *b, int64_t off, int64_t len) {
   }
 }
 
-int default_T(const heat_batch *b) { return b->dtype == HEAT_F32C ? 16 : 4; }
+int default_T(const heat_batch *b) { return b->dtype == HEAT_F32C ? 32 : 4; }
 
 struct Table {
   std::vector<BRing> rings;
@@ -428,8 +432,10 @@ int launch_table(heat_batch *b, const Table &t, int T) {
   a.wait_ns = b->wait_ns;
   const int64_t units = t.levp.back();
   const bool f32 = b->dtype == HEAT_F32C;
-  const int resident = f32 ? heat::resident_ctas<2>(b->sms) : heat::resident_ctas<0>(b->sms);
-  if (resident < 1) return HEAT_ECUDA;
+  int per_sm = f32 ? heat::per_sm_ctas<2>() : heat::per_sm_ctas<0>();
+  if (per_sm < 1) return HEAT_ECUDA;
+  if (b->ctas_per_sm > 0 && b->ctas_per_sm < per_sm) per_sm = b->ctas_per_sm;
+  const int resident = per_sm * b->sms;
   const int grid = (int)std::min<int64_t>(resident, units);
   const cudaError_t e = f32 ? heat::launch_batch<2>(a, grid, b->stream) : heat::launch_batch<0>(a, grid, b->stream);
   return e == cudaSuccess ? HEAT_OK : HEAT_ECUDA;
@@ -493,7 +499,7 @@ int heat_batch_create(heat_batch **out, int64_t capacity_points, heat_dtype dtyp
   b->dtype = dtype;
   b->elem = dtype == HEAT_F64 ? 8 : 4;
   b->capacity = round_up(capacity_points, kAlignPointsHost);
-  b->T = dtype == HEAT_F32C ? 16 : 4;
+  b->T = dtype == HEAT_F32C ? 32 : 4;
   int rc = HEAT_OK;
   if (cudaGetDevice(&b->device) != cudaSuccess ||
       cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, b->device) != cudaSuccess ||
@@ -655,10 +661,16 @@ int heat_batch_remove(heat_batch *b, int32_t ring_id) {
 
 int heat_batch_set_tuning(heat_batch *b, int T, int64_t seg_points) {
   if (!b || T < 0 || T > heat::kMaxT || seg_points < 0 || (seg_points > 0 && seg_points < 512)) return HEAT_EINVAL;
-  const int win = b->dtype == HEAT_F32C ? 32 * heat::tb::TB<2>::E : 32 * heat::tb::TB<0>::E;
+  const int win = b->dtype == HEAT_F32C ? 32 * heat::tb::TBC<2>::E : 32 * heat::tb::TBC<0>::E;
   if (T > 0 && 2 * T >= win) return HEAT_EINVAL;
   if (T > 0) b->T = T;
   if (seg_points > 0) b->seg_points = seg_points;
+  return HEAT_OK;
+}
+
+int heat_batch_set_ctas_per_sm(heat_batch *b, int ctas_per_sm) {
+  if (!b || ctas_per_sm < 0) return HEAT_EINVAL;
+  b->ctas_per_sm = ctas_per_sm;
   return HEAT_OK;
 }
 
@@ -775,7 +787,7 @@ int heat_batch_autotune(heat_batch *b, int *T_out, int64_t *seg_out) {
     }
   }
   const int Ts64[] = {2, 4, 8, 16};
-  const int Ts32[] = {8, 16, 32};
+  const int Ts32[] = {16, 32, 64};
   const int64_t segs[] = {4096, 16384, 65536};
   const int *Ts = b->dtype == HEAT_F32C ? Ts32 : Ts64;
   const int nT = b->dtype == HEAT_F32C ? 3 : 4;

@@ -1,0 +1,180 @@
+// k_cluster.cu -- form HEAT_FORM_CLUSTER: small rings in one thread-block
+// cluster, all nt steps in one launch.
+//
+// The ring is cut into C segments, one per CTA of a single cluster (C <= 16).
+// Each CTA keeps its segment in shared memory (two buffers).  Every block of T
+// steps, each warp builds a register window over its part of the segment plus a
+// T-point halo on each side; halo points come from the neighbouring CTAs'
+// shared memory through distributed shared memory (the cluster's ghost
+// exchange -- the GPU form of Section 2's neighbour queues, with the cluster
+// barrier as the only synchronisation), the window advances T steps with the
+// register-resident temporal-blocking core, and the exact middle is written to
+// the CTA's other buffer.  One cluster barrier per block orders the writes of
+// one block before the reads of the next and the reads of one block before the
+// writes that reuse its buffer.  The ring is periodic within the cluster: the
+// neighbours of CTA 0 are CTAs C-1 and 1.
+#include <cooperative_groups.h>
+
+#include "tb_core.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace heat {
+namespace {
+
+constexpr int kCWarps = 4;
+
+struct ClusterArgs {
+  const void *src;  // state at the start (global)
+  void *dst;        // state at the end (global)
+  int64_t N;
+  int C;            // CTAs (segments)
+  int T;
+  int64_t nt;
+  double r;
+  float rf;
+};
+
+template <int MODE>
+__global__ void __launch_bounds__(kCWarps * 32) k_cluster(ClusterArgs a) {
+  using P = tb::TBC<MODE>;
+  using Tt = typename P::T;
+  constexpr int E = P::E;
+  constexpr int WIN = 32 * E;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cg::cluster_group cluster = cg::this_cluster();
+  const int c = (int)cluster.block_rank();
+  const int lane = threadIdx.x & 31;
+  const int wib = threadIdx.x >> 5;
+  const int C = a.C;
+  const int64_t N = a.N;
+  // segment c: [lo, hi), balanced
+  const int64_t lo = (int64_t)c * N / C, hi = (int64_t)(c + 1) * N / C;
+  const int len = (int)(hi - lo);
+  const int cl = (c + C - 1) % C, cr = (c + 1) % C;
+  const int len_l = (int)(((int64_t)(cl + 1) * N / C) - ((int64_t)cl * N / C));
+  const int seg_max = (int)((N + C - 1) / C);
+  Tt *buf[2] = {reinterpret_cast<Tt *>(smem_raw), reinterpret_cast<Tt *>(smem_raw) + seg_max};
+
+  const Tt *src = (const Tt *)a.src;
+  for (int i = threadIdx.x; i < len; i += blockDim.x) buf[0][i] = src[lo + i];
+  cluster.sync();
+
+  const int W = WIN - 2 * a.T;
+  int cur = 0;
+  for (int64_t done = 0; done < a.nt;) {
+    const int steps = (int)(a.nt - done < a.T ? a.nt - done : a.T);
+    const Tt *own = buf[cur];
+    const Tt *left = cluster.map_shared_rank(buf[cur], cl);
+    const Tt *right = cluster.map_shared_rank(buf[cur], cr);
+    Tt *out = buf[cur ^ 1];
+    for (int w0 = wib * W; w0 < len; w0 += kCWarps * W) {
+      // window index i <-> segment-relative position p = w0 - T + i
+      typename P::Reg R;
+#pragma unroll
+      for (int k = 0; k < E; ++k) {
+        const int p = w0 - a.T + E * lane + k;
+        Tt v = Tt(0);  // points beyond the halo are never exact after T steps
+        if (C == 1) {  // the whole ring in one CTA: the window may wrap around it several times
+          int q = p % len;
+          if (q < 0) q += len;
+          v = own[q];
+        } else if (p < 0) {
+          if (p >= -a.T) v = left[len_l + p];
+        } else if (p < len) {
+          v = own[p];
+        } else if (p < len + a.T) {
+          v = right[p - len];
+        }
+        P::load(R, k, v);
+      }
+      for (int s = 0; s < steps; ++s) P::step(R, lane, a.r, a.rf);
+#pragma unroll
+      for (int k = 0; k < E; ++k) {
+        const int i = E * lane + k;
+        const int p = w0 - a.T + i;
+        if (i >= a.T && i < a.T + W && p < len) out[p] = P::store(R, k);
+      }
+    }
+    cluster.sync();  // this block's writes visible; its reads of `own` and the neighbours finished
+    cur ^= 1;
+    done += steps;
+  }
+  Tt *dst = (Tt *)a.dst;
+  for (int i = threadIdx.x; i < len; i += blockDim.x) dst[lo + i] = buf[cur][i];
+}
+
+template <int MODE>
+int launch_cluster(heat_ctx *c, int C, int T, int64_t nt) {
+  using P = tb::TBC<MODE>;
+  const int64_t N = c->geo.N;
+  const int seg_max = (int)((N + C - 1) / C);
+  const size_t smem = 2 * (size_t)seg_max * sizeof(typename P::T);
+  if (C > 8 &&
+      cudaFuncSetAttribute(k_cluster<MODE>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)
+    return HEAT_ECUDA;
+  if (cudaFuncSetAttribute(k_cluster<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    return HEAT_ECUDA;
+  ClusterArgs a;
+  a.src = c->buf[c->cur];
+  a.dst = c->buf[c->cur ^ 1];
+  a.N = N;
+  a.C = C;
+  a.T = T;
+  a.nt = nt;
+  a.r = c->r;
+  a.rf = c->rf;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(C);
+  cfg.blockDim = dim3(kCWarps * 32);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = c->stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = C;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int clusters = 0;
+  if (cudaOccupancyMaxActiveClusters(&clusters, k_cluster<MODE>, &cfg) != cudaSuccess || clusters < 1)
+    return HEAT_ENOTSUP;
+  return cudaLaunchKernelEx(&cfg, k_cluster<MODE>, a) == cudaSuccess ? HEAT_OK : HEAT_ECUDA;
+}
+
+}  // namespace
+
+// Largest ring the cluster form takes: 16 CTAs x 4 warps x one window output each.
+int64_t cluster_max_points(const heat_ctx *c, int T) {
+  const int win = c->dtype == HEAT_F32C ? 32 * tb::TBC<2>::E : 32 * tb::TBC<0>::E;
+  return (int64_t)16 * kCWarps * (win - 2 * T);
+}
+
+int run_cluster(heat_ctx *c, int64_t nt) {
+  const int mode = c->dtype == HEAT_F32C ? 2 : (c->arith == HEAT_ARITH_FMA ? 1 : 0);
+  const int T = c->T > 0 ? c->T : (c->dtype == HEAT_F32C ? 32 : 8);
+  const int64_t N = c->geo.N;
+  const int win = c->dtype == HEAT_F32C ? 32 * tb::TBC<2>::E : 32 * tb::TBC<0>::E;
+  if (2 * T >= win) return HEAT_EINVAL;
+  if (N > cluster_max_points(c, T)) return HEAT_ENOTSUP;
+  // as many CTAs as one window of output per CTA needs, at most 16, each
+  // segment at least T points long so a halo never reaches past a neighbour
+  // (a ring shorter than T runs in one CTA, whose windows wrap around it)
+  const int64_t W = win - 2 * T;
+  int64_t C = (N + W - 1) / W;
+  if (C > 16) C = 16;
+  while (C > 1 && N / C < T) --C;
+  if (C < 1) C = 1;
+  const int rc = mode == 0 ? launch_cluster<0>(c, (int)C, T, nt)
+                 : mode == 1 ? launch_cluster<1>(c, (int)C, T, nt)
+                             : launch_cluster<2>(c, (int)C, T, nt);
+  if (rc != HEAT_OK) return rc;
+  c->cur ^= 1;
+  c->steps += nt;
+  c->last_T = T;
+  c->last_launches = 1;
+  c->last_segments = (int)C;
+  return HEAT_OK;
+}
+
+}  // namespace heat

@@ -172,6 +172,50 @@ __global__ void __launch_bounds__(kWarps * 32) k_tblock(TBArgs a) {
   }
 }
 
+// Contiguous-ownership variant (lane l holds window points E*l .. E*l + E - 1):
+// two shuffles per carried value per lane and step instead of two per point.
+// Windows are loaded and stored with plain indexed accesses (wrapping around the
+// ring's ends where needed); tiles are claimed from the same launch-wide counter.
+template <int MODE>
+__global__ void __launch_bounds__(kWarps * 32) k_tblock_c(TBArgs a) {
+  using P = TBC<MODE>;
+  using T = typename P::T;
+  constexpr int E = P::E;
+  constexpr int WIN = 32 * E;
+  const int lane = threadIdx.x & 31;
+  const T *src = (const T *)a.src;
+  T *dst = (T *)a.dst;
+  const int64_t N = a.N;
+  const int W = WIN - 2 * a.T;
+  for (;;) {
+    unsigned long long t = 0;
+    if (lane == 0) t = atomicAdd(a.tile_counter, 1ull);
+    const int64_t tile = (int64_t)__shfl_sync(kFull, t, 0);
+    if (tile >= a.ntiles) break;
+    const int64_t ws = tile * (int64_t)W - a.T;
+    const int64_t base = ws + (int64_t)E * lane;
+    typename P::Reg R;
+    if (ws >= 0 && ws + WIN <= N) {
+#pragma unroll
+      for (int k = 0; k < E; ++k) P::load(R, k, src[base + k]);
+    } else {
+#pragma unroll
+      for (int k = 0; k < E; ++k) {
+        int64_t g = (base + k) % N;
+        if (g < 0) g += N;
+        P::load(R, k, src[g]);
+      }
+    }
+    for (int s = 0; s < a.steps; ++s) P::step(R, lane, a.r, a.rf);
+#pragma unroll
+    for (int k = 0; k < E; ++k) {
+      const int i = E * lane + k;
+      const int64_t g = ws + i;
+      if (i >= a.T && i < WIN - a.T && g < N) dst[g] = P::store(R, k);
+    }
+  }
+}
+
 template <int MODE>
 size_t smem_bytes() {
   using P = TB<MODE>;
@@ -210,6 +254,19 @@ int launch_tb(heat_ctx *c, const void *src, void *dst, int T, int steps) {
   for (int i = 0; i < 16; ++i)
     if (((i + 1) * j) / 16 > (i * j) / 16) a.add_mask |= 1u << i;
   const size_t smem = smem_bytes<MODE>();
+  if (c->tb_layout == 1) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tblock_c<MODE>, kWarps * 32, 0) != cudaSuccess ||
+        per_sm < 1)
+      return HEAT_ECUDA;
+    int64_t grid = (a.ntiles + kWarps - 1) / kWarps;
+    const int64_t cap = (int64_t)per_sm * c->sms;
+    if (grid > cap) grid = cap;
+    if (grid < 1) grid = 1;
+    if (cudaMemsetAsync(c->tile_counter, 0, sizeof(unsigned long long), c->stream) != cudaSuccess) return HEAT_ECUDA;
+    k_tblock_c<MODE><<<(int)grid, kWarps * 32, 0, c->stream>>>(a);
+    return cuda_status(cudaGetLastError());
+  }
   if (cudaFuncSetAttribute(k_tblock<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
     return HEAT_ECUDA;
   int per_sm = 0;
@@ -231,7 +288,7 @@ int tblock_window(int dtype) { return dtype == HEAT_F32C ? 32 * TB<2>::E : 32 * 
 
 int run_tblock(heat_ctx *c, int64_t nt) {
   const int mode = c->dtype == HEAT_F32C ? 2 : (c->arith == HEAT_ARITH_FMA ? 1 : 0);
-  int T = c->T > 0 ? c->T : (c->dtype == HEAT_F32C ? 16 : 4);
+  int T = c->T > 0 ? c->T : (c->dtype == HEAT_F32C ? 32 : 4);
   const int WIN = tblock_window(c->dtype);
   if (2 * T >= WIN) return HEAT_EINVAL;
   c->last_T = T;

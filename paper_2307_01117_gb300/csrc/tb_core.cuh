@@ -165,5 +165,72 @@ struct HasEmul {
   static constexpr bool value = MODE == 0;
 };
 
+// ---- contiguous ownership: lane l holds window points E*l .. E*l + E - 1 ------------------
+// A step needs only the last point of lane l-1 and the first point of lane l+1
+// (two shuffles per carried value per lane); every other neighbour is in the
+// lane's own registers.  Lane 0's left and lane 31's right neighbours are the
+// window's outer halo, which loses one valid point per step as in the strided
+// layout: after s steps the window points s .. WIN-1-s are exact.
+template <int MODE>
+struct TBC;
+
+template <int MODE>
+struct TBCf64 {
+  using T = double;
+  static constexpr int E = 16;  // window of 512
+  struct Reg {
+    double x[E];
+  };
+  static __device__ __forceinline__ void load(Reg &R, int k, double v) { R.x[k] = v; }
+  static __device__ __forceinline__ double store(const Reg &R, int k) { return R.x[k]; }
+  static __device__ __forceinline__ void step(Reg &R, int, double r, float) {
+    const double left = __shfl_up_sync(kFull, R.x[E - 1], 1);
+    const double right = __shfl_down_sync(kFull, R.x[0], 1);
+    double prev = left;
+#pragma unroll
+    for (int k = 0; k < E; ++k) {
+      const double nxt = k + 1 < E ? R.x[k + 1] : right;
+      const double v = eq2<MODE == 1>(prev, R.x[k], nxt, r);
+      prev = R.x[k];
+      R.x[k] = v;
+    }
+  }
+};
+template <>
+struct TBC<0> : TBCf64<0> {};
+template <>
+struct TBC<1> : TBCf64<1> {};
+
+template <>
+struct TBC<2> {
+  using T = float;
+  static constexpr int E = 32;  // window of 1024
+  struct Reg {
+    float h[E];
+    float l[E];
+  };
+  static __device__ __forceinline__ void load(Reg &R, int k, float v) {
+    R.h[k] = v;
+    R.l[k] = 0.0f;
+  }
+  static __device__ __forceinline__ float store(const Reg &R, int k) { return f32c_store(R.h[k], R.l[k]); }
+  static __device__ __forceinline__ void step(Reg &R, int, double, float rf) {
+    const float lh = __shfl_up_sync(kFull, R.h[E - 1], 1), ll = __shfl_up_sync(kFull, R.l[E - 1], 1);
+    const float rh = __shfl_down_sync(kFull, R.h[0], 1), rl = __shfl_down_sync(kFull, R.l[0], 1);
+    float ph = lh, pl = ll;
+#pragma unroll
+    for (int k = 0; k < E; ++k) {
+      const float nh = k + 1 < E ? R.h[k + 1] : rh;
+      const float nl = k + 1 < E ? R.l[k + 1] : rl;
+      float hn, ln;
+      eq2_f32c(ph, R.h[k], nh, pl, R.l[k], nl, rf, hn, ln);
+      ph = R.h[k];
+      pl = R.l[k];
+      R.h[k] = hn;
+      R.l[k] = ln;
+    }
+  }
+};
+
 }  // namespace tb
 }  // namespace heat

@@ -18,10 +18,11 @@ LIB_PATH = os.path.join(_PKG, "libheat.so")
 
 HEAT_F64, HEAT_F32C = 0, 1
 HEAT_OK, HEAT_EINVAL, HEAT_ENOMEM, HEAT_ECUDA, HEAT_ETIMEOUT, HEAT_ESTATE, HEAT_ENOTSUP = 0, -1, -2, -3, -4, -5, -6
-HEAT_FORM_PLAIN, HEAT_FORM_PERSIST, HEAT_FORM_TBLOCK, HEAT_FORM_AUTO = 0, 1, 2, 3
+HEAT_FORM_PLAIN, HEAT_FORM_PERSIST, HEAT_FORM_TBLOCK, HEAT_FORM_AUTO, HEAT_FORM_CLUSTER = 0, 1, 2, 3, 4
 HEAT_ARITH_EXACT, HEAT_ARITH_FMA = 0, 1
 
-FORMS = {"plain": HEAT_FORM_PLAIN, "persist": HEAT_FORM_PERSIST, "tblock": HEAT_FORM_TBLOCK, "auto": HEAT_FORM_AUTO}
+FORMS = {"plain": HEAT_FORM_PLAIN, "persist": HEAT_FORM_PERSIST, "tblock": HEAT_FORM_TBLOCK, "auto": HEAT_FORM_AUTO,
+         "cluster": HEAT_FORM_CLUSTER}
 DTYPES = {"f64": HEAT_F64, "f32c": HEAT_F32C}
 
 
@@ -51,6 +52,7 @@ _PROTOS = {
     "heat_set_segments": (_int, [_vp, _int]),
     "heat_set_emulation": (_int, [_vp, _int]),
     "heat_set_split": (_int, [_vp, _int]),
+    "heat_set_layout": (_int, [_vp, _int]),
     "heat_sum": (_int, [_vp, ctypes.POINTER(_d)]),
     "heat_steps": (_int, [_vp, ctypes.POINTER(_i64)]),
     "heat_last_run": (_int, [_vp, ctypes.POINTER(_int), ctypes.POINTER(_int), ctypes.POINTER(_i64),
@@ -72,6 +74,7 @@ _PROTOS = {
     "heat_batch_set_tuning": (_int, [_vp, _int, _i64]),
     "heat_batch_autotune": (_int, [_vp, ctypes.POINTER(_int), ctypes.POINTER(_i64)]),
     "heat_batch_set_stream": (_int, [_vp, _vp]),
+    "heat_batch_set_ctas_per_sm": (_int, [_vp, _int]),
     "heat_batch_save": (_int, [_vp]),
     "heat_batch_restore": (_int, [_vp]),
     "heat_batch_info": (_int, [_vp, ctypes.POINTER(_i32), ctypes.POINTER(_i64), ctypes.POINTER(_i64)]),
@@ -178,6 +181,10 @@ def heat_set_segments(ctx: int, segments: int) -> None:
 
 def heat_set_emulation(ctx: int, share: int) -> None:
     _check(lib().heat_set_emulation(ctx, int(share)), "heat_set_emulation")
+
+
+def heat_set_layout(ctx: int, layout: int) -> None:
+    _check(lib().heat_set_layout(ctx, int(layout)), "heat_set_layout")
 
 
 def heat_set_split(ctx: int, level: int) -> None:
@@ -306,6 +313,10 @@ def heat_batch_autotune(b: int) -> tuple[int, int]:
 def heat_batch_set_stream(b: int, stream) -> None:
     handle = None if stream is None else int(getattr(stream, "cuda_stream", stream))
     _check(lib().heat_batch_set_stream(b, handle), "heat_batch_set_stream")
+
+
+def heat_batch_set_ctas_per_sm(b: int, ctas: int) -> None:
+    _check(lib().heat_batch_set_ctas_per_sm(b, int(ctas)), "heat_batch_set_ctas_per_sm")
 
 
 def heat_batch_save(b: int) -> None:

@@ -73,7 +73,7 @@ class HeatServer:
     """budget_bytes: device memory for ring state (both arenas, both buffers)."""
 
     def __init__(self, budget_bytes: float, tick_steps: int = 256, lookahead: int = 64, f32c_share: float = 1 / 3,
-                 T64: int = 0, T32: int = 16, stream=None, init_fn=None):
+                 T64: int = 0, T32: int = 16, stream=None, init_fn=None, ctas64: int = 3, ctas32: int = 2):
         import torch
         self.torch = torch
         self.tick_steps = int(tick_steps)
@@ -83,9 +83,16 @@ class HeatServer:
         cap64 = max(1, int(budget_bytes * (1 - f32c_share)) // 16)
         self.caps = {False: cap64, True: cap32}
         self.batch = {False: H.heat_batch_create(cap64, H.HEAT_F64), True: H.heat_batch_create(cap32, H.HEAT_F32C)}
+        # one stream per arena: the binary64 batch (FP64 unit) and the binary32
+        # batch (FP32 and integer pipes) run side by side, each capped so that
+        # both fit on every SM
         self.stream = stream if stream is not None else torch.cuda.Stream()
-        for f32, b in self.batch.items():
-            H.heat_batch_set_stream(b, self.stream)
+        self.stream32 = torch.cuda.Stream()
+        H.heat_batch_set_stream(self.batch[False], self.stream)
+        H.heat_batch_set_stream(self.batch[True], self.stream32)
+        if ctas64 or ctas32:
+            H.heat_batch_set_ctas_per_sm(self.batch[False], ctas64)
+            H.heat_batch_set_ctas_per_sm(self.batch[True], ctas32)
         if T64:
             H.heat_batch_set_tuning(self.batch[False], T64, 0)
         H.heat_batch_set_tuning(self.batch[True], T32, 0)
@@ -122,7 +129,7 @@ class HeatServer:
             index, req = self.queue.popleft()
             looked += 1
             b = self.batch[req.f32c]
-            with self.torch.cuda.stream(self.stream):  # generate on the stream the copy is queued on
+            with self.torch.cuda.stream(self.stream32 if req.f32c else self.stream):  # the copy's stream
                 u = self.init_fn(req)
             try:
                 rid = H.heat_batch_add_device(b, req.n, 1, req.r, 1.0, 1.0, req.nt, u)

@@ -195,3 +195,21 @@ def test_tblock_rejects_depth_beyond_window():
         with pytest.raises(H.HeatError) as e:
             H.heat_set_form(h.ctx, 2, 65)         # beyond the library's maximum depth
         assert e.value.code == H.HEAT_EINVAL
+
+
+@pytest.mark.parametrize("dtype,T", [("f64", 1), ("f64", 4), ("f64", 9), ("f64", 64), ("f32c", 1), ("f32c", 16),
+                                     ("f32c", 33)])
+@pytest.mark.parametrize("n", [1, 5, 511, 513, 1024, 4000, 70001])
+def test_contiguous_layout_bitwise(dtype, T, n):
+    u0 = workloads.uniform(n, 60 + n, -1, 1)
+    nt = 2 * T + 3
+    with H.Heat(n, 1, 0.3, 1.0, 1.0, dtype=dtype, form="tblock", T=T) as h:
+        H.heat_set_layout(h.ctx, 1)
+        h.set(u0).run(nt)
+        got = h.get()
+    if dtype == "f64":
+        ref = oracle.run(u0, 0.3, nt)
+        assert same_bits(got, ref)
+    else:
+        ref = oracle.run_f32c(u0.astype(np.float32), np.float32(0.3), nt, T).astype(np.float64)
+        assert np.array_equal(got, ref)
