@@ -1,7 +1,7 @@
 """Benchmark of the periodic 1D heat stencil (Eq. 2, Section 2) on GB300.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
-                    [--form auto|plain|persist|tblock] [--T depth] [--arith exact|fma]
+                    [--form auto|plain|persist|tblock|cluster] [--T depth] [--arith exact|fma]
                     [--split L] [--emul S] [--impl ours|reference]
 
 Workloads (all synthetic, seeded; the paper's own workload is synthetic too):
@@ -283,16 +283,17 @@ class RingRunner:
         form = last["form"]
         launches = max(1, last["launches"])
         name = {"plain": "k_plain_f64" if self.w["dtype"] == "f64" else "k_plain_f32c", "persist": "k_persist",
-                "tblock": "k_tblock"}[form]
+                "tblock": "k_tblock", "cluster": "k_cluster"}[form]
         src = {"k_plain_f64": "k_plain.cu", "k_plain_f32c": "k_plain.cu", "k_persist": "k_persist.cu",
-               "k_tblock": "k_tblock.cu"}[name]
+               "k_tblock": "k_tblock.cu", "k_cluster": "k_cluster.cu"}[name]
         srcs = [f"paper_2307_01117_gb300/csrc/{src}", "paper_2307_01117_gb300/csrc/stencil_ops.cuh"]
-        if name == "k_tblock":
+        if name in ("k_tblock", "k_cluster"):
             srcs.append("paper_2307_01117_gb300/csrc/tb_core.cuh")
         steps_per_launch = self.nt / launches
         elem = 8.0 if self.w["dtype"] == "f64" else 4.0
         # every point read once and written once per launch; the persistent form
         # streams the ring through HBM once per step
+        # (the cluster form keeps the ring in shared memory: one read and one write per launch)
         alg_bytes = 2.0 * elem * self.n * (steps_per_launch if form == "persist" else 1.0)
         return {"kernel": name, "src": srcs, "launches": launches, "launch_ms": statistics.mean(run_ms) / launches,
                 "point_steps_per_launch": self.n * steps_per_launch, "alg_bytes_per_launch": alg_bytes,
@@ -508,7 +509,7 @@ def main() -> int:
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
-    ap.add_argument("--form", default="auto", choices=["auto", "plain", "persist", "tblock"])
+    ap.add_argument("--form", default="auto", choices=["auto", "plain", "persist", "tblock", "cluster"])
     ap.add_argument("--T", type=int, default=0)
     ap.add_argument("--arith", default="exact", choices=["exact", "fma"])
     ap.add_argument("--split", type=int, default=0)
