@@ -1,7 +1,7 @@
 """Benchmark of the periodic 1D heat stencil (Eq. 2, Section 2) on GB300.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
-                    [--form auto|plain|persist|tblock|cluster] [--T depth] [--arith exact|fma]
+                    [--form auto|plain|persist|tblock|cluster|persist_tb] [--T depth] [--arith exact|fma]
                     [--split L] [--emul S] [--impl ours|reference]
 
 Workloads (all synthetic, seeded; the paper's own workload is synthetic too):
@@ -180,6 +180,24 @@ def profile_traffic(kernel: str, workload: str, src_files: list[str]) -> float |
 
 
 # ---------------------------------------------------------------------------------------------
+# Replicas (N > 1): every rank runs the same workload on its own GPU
+
+def reduce_max(x: float, dist, device) -> float:
+    """Maximum of x over the ranks (x itself without a process group)."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(point_steps_per_step: float, steps: int, ms_max: float, world: int) -> float:
+    """Whole-job GLUP/s: all ranks' point-steps over the slowest rank's time."""
+    return world * point_steps_per_step * steps / (ms_max * 1e-3) / 1e9
+
+
+# ---------------------------------------------------------------------------------------------
 # CPU oracle baseline
 
 def cpu_baseline(w: dict, seconds: float = 12.0) -> dict:
@@ -283,18 +301,20 @@ class RingRunner:
         form = last["form"]
         launches = max(1, last["launches"])
         name = {"plain": "k_plain_f64" if self.w["dtype"] == "f64" else "k_plain_f32c", "persist": "k_persist",
-                "tblock": "k_tblock", "cluster": "k_cluster"}[form]
+                "tblock": "k_tblock", "cluster": "k_cluster", "persist_tb": "k_batch"}[form]
         src = {"k_plain_f64": "k_plain.cu", "k_plain_f32c": "k_plain.cu", "k_persist": "k_persist.cu",
-               "k_tblock": "k_tblock.cu", "k_cluster": "k_cluster.cu"}[name]
+               "k_tblock": "k_tblock.cu", "k_cluster": "k_cluster.cu", "k_batch": "k_batch.cu"}[name]
         srcs = [f"paper_2307_01117_gb300/csrc/{src}", "paper_2307_01117_gb300/csrc/stencil_ops.cuh"]
-        if name in ("k_tblock", "k_cluster"):
+        if name in ("k_tblock", "k_cluster", "k_batch"):
             srcs.append("paper_2307_01117_gb300/csrc/tb_core.cuh")
         steps_per_launch = self.nt / launches
         elem = 8.0 if self.w["dtype"] == "f64" else 4.0
         # every point read once and written once per launch; the persistent form
         # streams the ring through HBM once per step
-        # (the cluster form keeps the ring in shared memory: one read and one write per launch)
-        alg_bytes = 2.0 * elem * self.n * (steps_per_launch if form == "persist" else 1.0)
+        # (the cluster form keeps the ring in shared memory: one read and one write per launch;
+        # the persistent temporal-blocking form reads and writes the ring once per T-step level)
+        passes = {"persist": steps_per_launch, "persist_tb": -(-steps_per_launch // max(1, last["T"]))}.get(form, 1.0)
+        alg_bytes = 2.0 * elem * self.n * passes
         return {"kernel": name, "src": srcs, "launches": launches, "launch_ms": statistics.mean(run_ms) / launches,
                 "point_steps_per_launch": self.n * steps_per_launch, "alg_bytes_per_launch": alg_bytes,
                 "form": form, "T": last["T"], "segments": last["segments"] if form != "plain" else None}
@@ -509,7 +529,7 @@ def main() -> int:
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
-    ap.add_argument("--form", default="auto", choices=["auto", "plain", "persist", "tblock", "cluster"])
+    ap.add_argument("--form", default="auto", choices=["auto", "plain", "persist", "tblock", "cluster", "persist_tb"])
     ap.add_argument("--T", type=int, default=0)
     ap.add_argument("--arith", default="exact", choices=["exact", "fma"])
     ap.add_argument("--split", type=int, default=0)
@@ -554,11 +574,7 @@ def main() -> int:
             dist.barrier()
 
     def max_over_ranks(x: float) -> float:
-        if dist is None:
-            return x
-        t = torch.tensor([x], device=f"cuda:{local}")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return reduce_max(x, dist, torch.device("cuda", local))
 
     for _ in range(args.warmup):
         runner.step()
@@ -577,7 +593,7 @@ def main() -> int:
     clk = clocks.stop()
     ms_max = max_over_ranks(t_start.elapsed_time(t_end))
     run_ms = [a.elapsed_time(b) for a, b in evs]
-    value = world * runner.point_steps * args.steps / (ms_max * 1e-3) / 1e9
+    value = replica_throughput(runner.point_steps, args.steps, ms_max, world)
 
     # the dominant kernel: algorithmic work per launch over its average launch time
     ki = runner.kernel_info(run_ms)

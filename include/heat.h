@@ -72,13 +72,19 @@ typedef enum {
   HEAT_FORM_TBLOCK = 2,  /* temporal blocking: T steps per register-resident tile */
   HEAT_FORM_AUTO = 3,    /* library picks: HEAT_FORM_CLUSTER for small rings,
                             HEAT_FORM_TBLOCK otherwise */
-  HEAT_FORM_CLUSTER = 4  /* small rings (up to 16 x 4 windows of output, about
+  HEAT_FORM_CLUSTER = 4, /* small rings (up to 16 x 4 windows of output, about
                             31000 binary64 points at T = 8): one thread-block
                             cluster of up to 16 CTAs runs all nt steps in one
                             launch; each CTA keeps its segment in shared memory
                             and reads its neighbours' T-point halos through
                             distributed shared memory, one cluster barrier per
                             block of T steps */
+  HEAT_FORM_PERSIST_TB = 5 /* persistent temporal blocking: one launch for all
+                            nt steps; the ring is cut into segments that advance
+                            T steps at a time, each waiting (acquire/release
+                            flags, bounded) until it and its two neighbours
+                            finished the previous block -- the segmented
+                            algorithm of Section 2 with T-wide ghost zones */
 } heat_form;
 
 /* Rounding reading of Eq. 2 for HEAT_F64 (the paper states no order). */
@@ -175,6 +181,12 @@ int heat_set_split(heat_ctx *c, int level);
  * come from its own registers, so a step needs two shuffles per lane instead of
  * two per point; the default).  The state is bitwise the same for either layout. */
 int heat_set_layout(heat_ctx *c, int layout);
+
+/* CUDA graphs for the multi-launch forms (plain, temporal blocking), on by
+ * default: the first run with a given (form, T, nt, starting buffer,
+ * arithmetic, layout, stream) is captured into a graph, later identical runs
+ * replay it.  Runs of more than 8192 launches are not captured. */
+int heat_set_graphs(heat_ctx *c, int enable);
 
 /* Select the rounding reading for HEAT_F64 (heat_arith).  HEAT_F32C ignores it. */
 int heat_set_arith(heat_ctx *c, int arith);

@@ -1,12 +1,24 @@
 // heat_api.cu -- the C ABI of include/heat.h: context lifetime, argument
 // validation, state transfer and dispatch to the kernel forms.
 #include <math.h>
+#include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+
+#include <nvtx3/nvToolsExt.h>
+#include <stdio.h>
 
 #include "heat_internal.cuh"
 
 using heat::DevStatus;
+
+namespace {
+// NVTX range over a host call (visible in Nsight timelines; a no-op without a tool).
+struct NvtxRange {
+  explicit NvtxRange(const char *msg) { nvtxRangePushA(msg); }
+  ~NvtxRange() { nvtxRangePop(); }
+};
+}  // namespace
 
 namespace {
 
@@ -30,6 +42,8 @@ void free_ctx(heat_ctx *c) {
   if (c->partials) cudaFree(c->partials);
   if (c->hsum) cudaFreeHost(c->hsum);
   if (c->tile_counter) cudaFree(c->tile_counter);
+  if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+  heat::free_persist_tb(c);
   if (c->own_stream) cudaStreamDestroy(c->own_stream);
   free(c);
 }
@@ -51,6 +65,64 @@ int reset_status(heat_ctx *c) {
 }
 
 }  // namespace
+
+// Multi-launch runs (one launch per step or per T steps) are captured into a
+// CUDA graph the first time and replayed while the run key -- form, depth,
+// steps, starting buffer, arithmetic, layout, stream -- stays the same: the
+// launches then cost one graph launch instead of one host call each.
+int run_graphed(heat_ctx *c, int form, int64_t nt) {
+  const int T = c->T;
+  const int64_t depth = form == HEAT_FORM_PLAIN ? 1 : (T > 0 ? T : (c->dtype == HEAT_F32C ? 32 : 4));
+  if ((nt + depth - 1) / depth > 8192) return HEAT_ENOTSUP;  // keep graphs small
+  const unsigned long long key[8] = {(unsigned long long)form, (unsigned long long)T, (unsigned long long)nt,
+                                     (unsigned long long)c->cur, (unsigned long long)c->arith,
+                                     (unsigned long long)c->tb_layout,
+                                     ((unsigned long long)c->split_level << 32) | c->emul_mask,
+                                     (unsigned long long)(uintptr_t)c->stream};
+  if (c->graph_exec && memcmp(key, c->graph_key, sizeof(key)) == 0) {
+    if (cudaGraphLaunch(c->graph_exec, c->stream) != cudaSuccess) return HEAT_ECUDA;
+    c->cur ^= c->graph_cur_flip;
+    c->steps += nt;
+    c->last_T = c->graph_last_T;
+    c->last_launches = c->graph_last_launches;
+    return HEAT_OK;
+  }
+  if (c->graph_exec) {
+    cudaGraphExecDestroy(c->graph_exec);
+    c->graph_exec = nullptr;
+  }
+  const int cur0 = c->cur;
+  const int64_t steps0 = c->steps;
+  if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaGetLastError();
+    return HEAT_ENOTSUP;
+  }
+  const int rc = form == HEAT_FORM_PLAIN ? heat::run_plain(c, nt) : heat::run_tblock(c, nt);
+  cudaGraph_t graph = nullptr;
+  const cudaError_t ec = cudaStreamEndCapture(c->stream, &graph);
+  cudaGraphExec_t exec = nullptr;
+  if (rc != HEAT_OK || ec != cudaSuccess || !graph ||
+      cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();
+    c->cur = cur0;  // nothing ran
+    c->steps = steps0;
+    return rc != HEAT_OK ? rc : HEAT_ENOTSUP;
+  }
+  cudaGraphDestroy(graph);
+  if (cudaGraphLaunch(exec, c->stream) != cudaSuccess) {
+    cudaGraphExecDestroy(exec);
+    c->cur = cur0;
+    c->steps = steps0;
+    return HEAT_ECUDA;
+  }
+  c->graph_exec = exec;
+  memcpy(c->graph_key, key, sizeof(key));
+  c->graph_cur_flip = c->cur ^ cur0;
+  c->graph_last_T = c->last_T;
+  c->graph_last_launches = c->last_launches;
+  return HEAT_OK;
+}
 
 extern "C" {
 
@@ -85,6 +157,7 @@ int heat_create(heat_ctx **out, int64_t nx, int32_t np, double k, double dt, dou
   heat_set_emulation(c, kDefaultEmulShare);
   heat_set_split(c, kDefaultSplit);
   c->tb_layout = 1;  // contiguous per-lane ownership (measured fastest for both dtypes)
+  c->graphs = 1;
   int rc = HEAT_OK;
   if (cudaGetDevice(&c->device) != cudaSuccess ||
       cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess) {
@@ -203,6 +276,10 @@ int heat_run(heat_ctx *c, int64_t nt) {
   if (!c || nt < 0) return HEAT_EINVAL;
   if (c->host_error != HEAT_OK) return HEAT_ESTATE;
   if (nt == 0) return HEAT_OK;
+  char label[96];
+  snprintf(label, sizeof(label), "heat_run nt=%lld N=%lld form=%d T=%d", (long long)nt, (long long)c->geo.N,
+           c->form, c->T);
+  NvtxRange range(label);
   int form = c->form;
   // default: one cluster launch for small rings (latency-bound: one launch for
   // all steps, ghost exchange through distributed shared memory), temporal
@@ -212,11 +289,16 @@ int heat_run(heat_ctx *c, int64_t nt) {
   c->last_form = form;
   c->last_T = 1;
   c->last_launches = 0;
+  if (c->graphs && (form == HEAT_FORM_PLAIN || form == HEAT_FORM_TBLOCK)) {
+    const int rc = run_graphed(c, form, nt);
+    if (rc != HEAT_ENOTSUP) return rc;  // HEAT_ENOTSUP: not graphable, run directly
+  }
   switch (form) {
     case HEAT_FORM_PLAIN: return heat::run_plain(c, nt);
     case HEAT_FORM_PERSIST: return heat::run_persist(c, nt);
     case HEAT_FORM_TBLOCK: return heat::run_tblock(c, nt);
     case HEAT_FORM_CLUSTER: return heat::run_cluster(c, nt);
+    case HEAT_FORM_PERSIST_TB: return heat::run_persist_tb(c, nt);
     default: return HEAT_EINVAL;
   }
 }
@@ -251,10 +333,16 @@ int heat_set_stream(heat_ctx *c, void *cuda_stream) {
 
 int heat_set_form(heat_ctx *c, int form, int T) {
   if (!c) return HEAT_EINVAL;
-  if (form < HEAT_FORM_PLAIN || form > HEAT_FORM_CLUSTER) return HEAT_EINVAL;
+  if (form < HEAT_FORM_PLAIN || form > HEAT_FORM_PERSIST_TB) return HEAT_EINVAL;
   if (T < 0 || T > heat::kMaxT) return HEAT_EINVAL;
   c->form = form;
   c->T = T;
+  return HEAT_OK;
+}
+
+int heat_set_graphs(heat_ctx *c, int enable) {
+  if (!c) return HEAT_EINVAL;
+  c->graphs = enable ? 1 : 0;
   return HEAT_OK;
 }
 

@@ -42,6 +42,8 @@ struct Geometry {
 
 }  // namespace heat
 
+struct heat_batch;
+
 struct heat_ctx {
   heat::Geometry geo;
   double r;          // k*dt/(dx*dx), binary64
@@ -73,6 +75,15 @@ struct heat_ctx {
   unsigned emul_mask;            // the same as a bit mask over tile index mod 32
   int split_level;               // per-point split of the binary64 update between FP64 unit and integer pipes
   int tb_layout;                 // temporal-blocking register layout: 0 strided (TMA-staged), 1 contiguous
+  heat_batch *ptb;               // work-table state of the persistent temporal-blocking form (lazy)
+  // CUDA graph of the last multi-launch run (plain / temporal blocking), replayed
+  // when the next run has the same key
+  int graphs;                    // 1: capture and replay multi-launch runs
+  cudaGraphExec_t graph_exec;
+  unsigned long long graph_key[8];
+  int graph_cur_flip;            // parity change of the current buffer over the run
+  int graph_last_T;
+  int64_t graph_last_launches;
   double *partials;              // reduction scratch, device
   unsigned long long *tile_counter;  // dynamic tile counter of the temporal-blocking form, device
   double *hsum;                  // pinned host word for heat_sum
@@ -88,6 +99,8 @@ int run_plain(heat_ctx *c, int64_t nt);
 int run_persist(heat_ctx *c, int64_t nt);
 int run_tblock(heat_ctx *c, int64_t nt);
 int run_cluster(heat_ctx *c, int64_t nt);
+int run_persist_tb(heat_ctx *c, int64_t nt);
+void free_persist_tb(heat_ctx *c);
 int64_t cluster_max_points(const heat_ctx *c, int T);
 int sum_state(heat_ctx *c, double *out);
 int convert_f64_to_state(heat_ctx *c, const double *dev_src, void *dev_dst, int64_t n);

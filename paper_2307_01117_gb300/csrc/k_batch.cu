@@ -837,3 +837,74 @@ int heat_batch_autotune(heat_batch *b, int *T_out, int64_t *seg_out) {
 }
 
 }  // extern "C"
+
+namespace heat {
+
+// HEAT_FORM_PERSIST_TB for a single ring: the work-table kernel over one ring
+// whose two buffers are the context's own, segments sized so that the levels
+// keep every CTA busy.  One launch advances all nt steps.
+int run_persist_tb(heat_ctx *c, int64_t nt) {
+  if (!c->ptb) {
+    heat_batch *b = new (std::nothrow) heat_batch();
+    if (!b) return HEAT_ENOMEM;
+    b->dtype = c->dtype;
+    b->elem = c->elem;
+    b->device = c->device;
+    b->sms = c->sms;
+    b->dstat = c->dstat;  // shared with the context: its errors surface at heat_sync
+    if (cudaEventCreateWithFlags(&b->staged, cudaEventDisableTiming) != cudaSuccess ||
+        cudaMalloc((void **)&b->d_counter, sizeof(unsigned long long)) != cudaSuccess) {
+      if (b->staged) cudaEventDestroy(b->staged);
+      delete b;
+      return HEAT_ENOMEM;
+    }
+    c->ptb = b;
+  }
+  heat_batch *b = c->ptb;
+  b->stream = c->stream;
+  b->arena[0] = c->buf[0];
+  b->arena[1] = c->buf[1];
+  b->wait_ns = c->wait_ns;
+  const int T = c->T > 0 ? c->T : (c->dtype == HEAT_F32C ? 32 : 4);
+  const int win = c->dtype == HEAT_F32C ? 32 * tb::TBC<2>::E : 32 * tb::TBC<0>::E;
+  if (2 * T >= win) return HEAT_EINVAL;
+  heat_batch::Ring r;
+  r.live = true;
+  r.off = 0;
+  r.n = c->geo.N;
+  r.len = c->geo.N;
+  r.r = c->r;
+  r.rf = c->rf;
+  r.nt = nt;
+  r.parity = c->cur;
+  b->rings.assign(1, r);
+  // about three segments per resident CTA, each at least 512 points
+  const int64_t per_sm = c->dtype == HEAT_F32C ? 3 : 5;
+  int64_t seg = c->geo.N / (3 * per_sm * c->sms);
+  if (seg < 512) seg = 512;
+  Table t = build_table(b, T, seg, [&](const heat_batch::Ring &rr) { return rr.nt; });
+  const int rc = launch_table(b, t, T);
+  if (rc != HEAT_OK) return rc;
+  const int64_t levels = (nt + T - 1) / T;
+  if (levels & 1) c->cur ^= 1;
+  c->steps += nt;
+  c->last_T = T;
+  c->last_launches = 1;
+  c->last_segments = (int)t.rings[0].nseg;
+  return HEAT_OK;
+}
+
+void free_persist_tb(heat_ctx *c) {
+  heat_batch *b = c->ptb;
+  if (!b) return;
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  if (b->d_blob) cudaFree(b->d_blob);
+  if (b->d_done) cudaFree(b->d_done);
+  if (b->d_counter) cudaFree(b->d_counter);
+  if (b->h_stage) cudaFreeHost(b->h_stage);
+  if (b->staged) cudaEventDestroy(b->staged);
+  delete b;
+  c->ptb = nullptr;
+}
+
+}  // namespace heat

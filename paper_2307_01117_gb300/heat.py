@@ -19,10 +19,11 @@ LIB_PATH = os.path.join(_PKG, "libheat.so")
 HEAT_F64, HEAT_F32C = 0, 1
 HEAT_OK, HEAT_EINVAL, HEAT_ENOMEM, HEAT_ECUDA, HEAT_ETIMEOUT, HEAT_ESTATE, HEAT_ENOTSUP = 0, -1, -2, -3, -4, -5, -6
 HEAT_FORM_PLAIN, HEAT_FORM_PERSIST, HEAT_FORM_TBLOCK, HEAT_FORM_AUTO, HEAT_FORM_CLUSTER = 0, 1, 2, 3, 4
+HEAT_FORM_PERSIST_TB = 5
 HEAT_ARITH_EXACT, HEAT_ARITH_FMA = 0, 1
 
 FORMS = {"plain": HEAT_FORM_PLAIN, "persist": HEAT_FORM_PERSIST, "tblock": HEAT_FORM_TBLOCK, "auto": HEAT_FORM_AUTO,
-         "cluster": HEAT_FORM_CLUSTER}
+         "cluster": HEAT_FORM_CLUSTER, "persist_tb": HEAT_FORM_PERSIST_TB}
 DTYPES = {"f64": HEAT_F64, "f32c": HEAT_F32C}
 
 
@@ -53,6 +54,7 @@ _PROTOS = {
     "heat_set_emulation": (_int, [_vp, _int]),
     "heat_set_split": (_int, [_vp, _int]),
     "heat_set_layout": (_int, [_vp, _int]),
+    "heat_set_graphs": (_int, [_vp, _int]),
     "heat_sum": (_int, [_vp, ctypes.POINTER(_d)]),
     "heat_steps": (_int, [_vp, ctypes.POINTER(_i64)]),
     "heat_last_run": (_int, [_vp, ctypes.POINTER(_int), ctypes.POINTER(_int), ctypes.POINTER(_i64),
@@ -181,6 +183,10 @@ def heat_set_segments(ctx: int, segments: int) -> None:
 
 def heat_set_emulation(ctx: int, share: int) -> None:
     _check(lib().heat_set_emulation(ctx, int(share)), "heat_set_emulation")
+
+
+def heat_set_graphs(ctx: int, enable: bool) -> None:
+    _check(lib().heat_set_graphs(ctx, int(bool(enable))), "heat_set_graphs")
 
 
 def heat_set_layout(ctx: int, layout: int) -> None:

@@ -17,8 +17,10 @@ from paper_2307_01117_gb300 import workloads
 
 pytestmark = pytest.mark.gpu
 
-FORMS_F64 = [("plain", 0), ("persist", 0), ("tblock", 1), ("tblock", 4), ("tblock", 7), ("tblock", 64)]
-FORMS_F32C = [("plain", 0), ("persist", 0), ("tblock", 1), ("tblock", 8), ("tblock", 13), ("tblock", 64)]
+FORMS_F64 = [("plain", 0), ("persist", 0), ("tblock", 1), ("tblock", 4), ("tblock", 7), ("tblock", 64),
+             ("persist_tb", 1), ("persist_tb", 4), ("persist_tb", 13)]
+FORMS_F32C = [("plain", 0), ("persist", 0), ("tblock", 1), ("tblock", 8), ("tblock", 13), ("tblock", 64),
+              ("persist_tb", 8), ("persist_tb", 32)]
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -89,7 +91,7 @@ def test_f32c_bitwise(form, T, n):
     u0 = workloads.uniform(n, 5 + n, -1, 1)
     u32 = u0.astype(np.float32)
     for nt, r in [(1, 0.5), (13, 0.3), (40, 0.25)]:
-        Tb = T if form == "tblock" else 1
+        Tb = T if form in ("tblock", "persist_tb") else 1
         ref = oracle.run_f32c(u32, np.float32(r), nt, max(Tb, 1)).astype(np.float64)
         got = run_gpu(u0, 1, r, nt, form, T, dtype="f32c")
         assert np.array_equal(got, ref), (n, nt, r)
@@ -213,3 +215,20 @@ def test_contiguous_layout_bitwise(dtype, T, n):
     else:
         ref = oracle.run_f32c(u0.astype(np.float32), np.float32(0.3), nt, T).astype(np.float64)
         assert np.array_equal(got, ref)
+
+
+@pytest.mark.parametrize("form,T", [("plain", 0), ("tblock", 4), ("tblock", 0)])
+def test_graph_replay_matches_direct_launches(form, T):
+    """The second identical run replays the captured CUDA graph."""
+    u0 = workloads.uniform(50000, 8, -1, 1)
+    ref = oracle.run(u0, 0.3, 33)
+    with H.Heat(50000, 1, 0.3, 1.0, 1.0, form=form, T=T) as h:
+        outs = []
+        for _ in range(3):
+            h.set(u0).run(33)
+            outs.append(h.get())
+        H.heat_set_graphs(h.ctx, False)
+        h.set(u0).run(33)
+        outs.append(h.get())
+    for o in outs:
+        assert same_bits(o, ref)
