@@ -9,7 +9,7 @@ Workloads (all synthetic, seeded; the paper's own workload is synthetic too):
                   u0 = U[0,1) + sin(2 pi 3 g / N)
   ring-1e6-f64    the paper's shape (Section 6): 10^6 points, 1000 steps, u0 = g
   ring-4000-f64   np = 4 x nx = 1000, nt = 100, r = 0.5, u0 = g
-  ring-2^25-f64   profiling case (still larger than L2)
+  ring-2^25-f64   profiling case (still larger than L2); ring-2^25-f32c likewise
   ring-2^28-f32c  binary32 compensated state, u0 = sum of modes 1, 7, 64
   batch-4096-f64  4096 independent rings, N log-uniform in [1e3, 1e6], np in
                   {1,2,4,8,16}, nt uniform in [100, 5000], r uniform in
@@ -59,6 +59,8 @@ WORKLOADS = {
     "ring-4000-f64": dict(kind="ring", nx=1000, np=4, nt=100, k=0.5, dt=1.0, dx=1.0, init="ramp", dtype="f64"),
     "ring-2^25-f64": dict(kind="ring", nx=1 << 20, np=32, nt=20, k=0.25, dt=1.0, dx=1.0, init="uniform+mode3",
                           dtype="f64"),
+    "ring-2^25-f32c": dict(kind="ring", nx=1 << 20, np=32, nt=64, k=0.25, dt=1.0, dx=1.0, init="modes1,7,64",
+                           dtype="f32c"),
     "ring-2^28-f32c": dict(kind="ring", nx=1 << 20, np=256, nt=1000, k=0.25, dt=1.0, dx=1.0, init="modes1,7,64",
                            dtype="f32c"),
     "batch-4096-f64": dict(kind="batch", count=4096, seed=1, dtype="f64"),

@@ -118,7 +118,7 @@ __device__ __forceinline__ int64_t floor_index(const int64_t *v, int64_t lo, int
 }
 
 template <int MODE>
-__global__ void __launch_bounds__(kBWarps * 32, MODE == 2 ? 3 : 5) k_batch(BatchArgs a) {
+__global__ void __launch_bounds__(kBWarps * 32, MODE == 2 ? 3 : 5) k_batch(BatchArgs a) {  // MODE: 0 exact, 1 fused, 2 binary32
   using P = tb::TBC<MODE>;  // contiguous per-lane ownership
   using T = typename P::T;
   constexpr int E = P::E;
@@ -260,6 +260,7 @@ struct heat_batch {
   cudaEvent_t staged = nullptr;
   bool staged_pending = false;
   int T = 0;
+  int arith = HEAT_ARITH_EXACT;  // binary64 reading (the batch API is exact; the persistent form passes its own)
   int ctas_per_sm = 0;  // 0: as many as fit
   int64_t seg_points = 16384;
   int64_t last_point_steps = 0;
@@ -432,12 +433,15 @@ int launch_table(heat_batch *b, const Table &t, int T) {
   a.wait_ns = b->wait_ns;
   const int64_t units = t.levp.back();
   const bool f32 = b->dtype == HEAT_F32C;
-  int per_sm = f32 ? heat::per_sm_ctas<2>() : heat::per_sm_ctas<0>();
+  const bool fma = !f32 && b->arith == HEAT_ARITH_FMA;
+  int per_sm = f32 ? heat::per_sm_ctas<2>() : fma ? heat::per_sm_ctas<1>() : heat::per_sm_ctas<0>();
   if (per_sm < 1) return HEAT_ECUDA;
   if (b->ctas_per_sm > 0 && b->ctas_per_sm < per_sm) per_sm = b->ctas_per_sm;
   const int resident = per_sm * b->sms;
   const int grid = (int)std::min<int64_t>(resident, units);
-  const cudaError_t e = f32 ? heat::launch_batch<2>(a, grid, b->stream) : heat::launch_batch<0>(a, grid, b->stream);
+  const cudaError_t e = f32   ? heat::launch_batch<2>(a, grid, b->stream)
+                        : fma ? heat::launch_batch<1>(a, grid, b->stream)
+                              : heat::launch_batch<0>(a, grid, b->stream);
   return e == cudaSuccess ? HEAT_OK : HEAT_ECUDA;
 }
 
@@ -862,6 +866,7 @@ int run_persist_tb(heat_ctx *c, int64_t nt) {
   }
   heat_batch *b = c->ptb;
   b->stream = c->stream;
+  b->arith = c->arith;
   b->arena[0] = c->buf[0];
   b->arena[1] = c->buf[1];
   b->wait_ns = c->wait_ns;

@@ -35,9 +35,9 @@ struct ClusterArgs {
   float rf;
 };
 
-template <int MODE>
+template <int MODE, int EP>
 __global__ void __launch_bounds__(kCWarps * 32) k_cluster(ClusterArgs a) {
-  using P = tb::TBC<MODE>;
+  using P = tb::TBCx<MODE, EP>;
   using Tt = typename P::T;
   constexpr int E = P::E;
   constexpr int WIN = 32 * E;
@@ -104,16 +104,17 @@ __global__ void __launch_bounds__(kCWarps * 32) k_cluster(ClusterArgs a) {
   for (int i = threadIdx.x; i < len; i += blockDim.x) dst[lo + i] = buf[cur][i];
 }
 
-template <int MODE>
+template <int MODE, int EP>
 int launch_cluster(heat_ctx *c, int C, int T, int64_t nt) {
-  using P = tb::TBC<MODE>;
+  using P = tb::TBCx<MODE, EP>;
   const int64_t N = c->geo.N;
   const int seg_max = (int)((N + C - 1) / C);
   const size_t smem = 2 * (size_t)seg_max * sizeof(typename P::T);
   if (C > 8 &&
-      cudaFuncSetAttribute(k_cluster<MODE>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)
+      cudaFuncSetAttribute(k_cluster<MODE, EP>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)
     return HEAT_ECUDA;
-  if (cudaFuncSetAttribute(k_cluster<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+  if (cudaFuncSetAttribute(k_cluster<MODE, EP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+      cudaSuccess)
     return HEAT_ECUDA;
   ClusterArgs a;
   a.src = c->buf[c->cur];
@@ -137,16 +138,39 @@ int launch_cluster(heat_ctx *c, int C, int T, int64_t nt) {
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   int clusters = 0;
-  if (cudaOccupancyMaxActiveClusters(&clusters, k_cluster<MODE>, &cfg) != cudaSuccess || clusters < 1)
+  if (cudaOccupancyMaxActiveClusters(&clusters, k_cluster<MODE, EP>, &cfg) != cudaSuccess || clusters < 1)
     return HEAT_ENOTSUP;
-  return cudaLaunchKernelEx(&cfg, k_cluster<MODE>, a) == cudaSuccess ? HEAT_OK : HEAT_ECUDA;
+  return cudaLaunchKernelEx(&cfg, k_cluster<MODE, EP>, a) == cudaSuccess ? HEAT_OK : HEAT_ECUDA;
+}
+
+// Points per lane the cluster form may use, smallest first (smaller windows
+// spread a small ring over more warps, hence more of each SM's FP64 unit).
+constexpr int kEp64[3] = {4, 8, 16};
+constexpr int kEp32[3] = {8, 16, 32};
+
+template <int MODE>
+int launch_ep(heat_ctx *c, int ep, int C, int T, int64_t nt) {
+  if constexpr (MODE == 2) {
+    switch (ep) {
+      case 8: return launch_cluster<MODE, 8>(c, C, T, nt);
+      case 16: return launch_cluster<MODE, 16>(c, C, T, nt);
+      default: return launch_cluster<MODE, 32>(c, C, T, nt);
+    }
+  } else {
+    switch (ep) {
+      case 4: return launch_cluster<MODE, 4>(c, C, T, nt);
+      case 8: return launch_cluster<MODE, 8>(c, C, T, nt);
+      default: return launch_cluster<MODE, 16>(c, C, T, nt);
+    }
+  }
 }
 
 }  // namespace
 
-// Largest ring the cluster form takes: 16 CTAs x 4 warps x one window output each.
+// Largest ring the cluster form takes: 16 CTAs x 4 warps x one window of output
+// each, at the largest window.
 int64_t cluster_max_points(const heat_ctx *c, int T) {
-  const int win = c->dtype == HEAT_F32C ? 32 * tb::TBC<2>::E : 32 * tb::TBC<0>::E;
+  const int win = c->dtype == HEAT_F32C ? 32 * kEp32[2] : 32 * kEp64[2];
   return (int64_t)16 * kCWarps * (win - 2 * T);
 }
 
@@ -154,20 +178,29 @@ int run_cluster(heat_ctx *c, int64_t nt) {
   const int mode = c->dtype == HEAT_F32C ? 2 : (c->arith == HEAT_ARITH_FMA ? 1 : 0);
   const int T = c->T > 0 ? c->T : (c->dtype == HEAT_F32C ? 32 : 8);
   const int64_t N = c->geo.N;
-  const int win = c->dtype == HEAT_F32C ? 32 * tb::TBC<2>::E : 32 * tb::TBC<0>::E;
-  if (2 * T >= win) return HEAT_EINVAL;
+  const int *eps = c->dtype == HEAT_F32C ? kEp32 : kEp64;
+  if (2 * T >= 32 * eps[2]) return HEAT_EINVAL;
   if (N > cluster_max_points(c, T)) return HEAT_ENOTSUP;
-  // as many CTAs as one window of output per CTA needs, at most 16, each
-  // segment at least T points long so a halo never reaches past a neighbour
-  // (a ring shorter than T runs in one CTA, whose windows wrap around it)
-  const int64_t W = win - 2 * T;
+  // the smallest window whose 64 copies (16 CTAs x 4 warps) cover the ring
+  int ep = eps[2];
+  for (int i = 0; i < 3; ++i) {
+    const int64_t w = 32 * eps[i] - 2 * T;
+    if (w >= T && w * 16 * kCWarps >= N) {
+      ep = eps[i];
+      break;
+    }
+  }
+  const int64_t W = 32 * ep - 2 * T;
+  // one window of output per CTA at least, at most 16 CTAs, each segment at
+  // least T points long so a halo never reaches past a neighbour (a ring
+  // shorter than T runs in one CTA, whose windows wrap around it)
   int64_t C = (N + W - 1) / W;
   if (C > 16) C = 16;
   while (C > 1 && N / C < T) --C;
   if (C < 1) C = 1;
-  const int rc = mode == 0 ? launch_cluster<0>(c, (int)C, T, nt)
-                 : mode == 1 ? launch_cluster<1>(c, (int)C, T, nt)
-                             : launch_cluster<2>(c, (int)C, T, nt);
+  const int rc = mode == 0 ? launch_ep<0>(c, ep, (int)C, T, nt)
+                 : mode == 1 ? launch_ep<1>(c, ep, (int)C, T, nt)
+                             : launch_ep<2>(c, ep, (int)C, T, nt);
   if (rc != HEAT_OK) return rc;
   c->cur ^= 1;
   c->steps += nt;

@@ -171,13 +171,14 @@ struct HasEmul {
 // lane's own registers.  Lane 0's left and lane 31's right neighbours are the
 // window's outer halo, which loses one valid point per step as in the strided
 // layout: after s steps the window points s .. WIN-1-s are exact.
-template <int MODE>
-struct TBC;
+template <int MODE, int EP>
+struct TBCx;
 
-template <int MODE>
+// binary64 (MODE 0 exact reading, 1 fused reading), EP points per lane
+template <int MODE, int EP>
 struct TBCf64 {
   using T = double;
-  static constexpr int E = 16;  // window of 512
+  static constexpr int E = EP;
   struct Reg {
     double x[E];
   };
@@ -196,15 +197,16 @@ struct TBCf64 {
     }
   }
 };
-template <>
-struct TBC<0> : TBCf64<0> {};
-template <>
-struct TBC<1> : TBCf64<1> {};
+template <int EP>
+struct TBCx<0, EP> : TBCf64<0, EP> {};
+template <int EP>
+struct TBCx<1, EP> : TBCf64<1, EP> {};
 
-template <>
-struct TBC<2> {
+// binary32 compensated, EP points per lane
+template <int EP>
+struct TBCx<2, EP> {
   using T = float;
-  static constexpr int E = 32;  // window of 1024
+  static constexpr int E = EP;
   struct Reg {
     float h[E];
     float l[E];
@@ -231,6 +233,10 @@ struct TBC<2> {
     }
   }
 };
+
+// Default window: 512 binary64 points, 1024 binary32 points.
+template <int MODE>
+struct TBC : TBCx<MODE, MODE == 2 ? 32 : 16> {};
 
 }  // namespace tb
 }  // namespace heat
