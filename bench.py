@@ -2,7 +2,7 @@
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
                     [--form auto|plain|persist|tblock|cluster|persist_tb] [--T depth] [--arith exact|fma]
-                    [--split L] [--emul S] [--impl ours|reference]
+                    [--layout 0|1] [--split L] [--emul S] [--impl ours|reference]
 
 Workloads (all synthetic, seeded; the paper's own workload is synthetic too):
   ring-2^28-f64   (default) one ring, np = 256 x nx = 2^20, nt = 1000, r = 0.25,
@@ -267,6 +267,8 @@ class RingRunner:
         arith = H.HEAT_ARITH_FMA if args.arith == "fma" else H.HEAT_ARITH_EXACT
         self.h = H.Heat(w["nx"], w["np"], w["k"], w["dt"], w["dx"], dtype=w["dtype"], form=args.form, T=args.T,
                         arith=arith, stream=stream)
+        if args.layout >= 0:
+            H.heat_set_layout(self.h.ctx, args.layout)
         if args.split:
             H.heat_set_split(self.h.ctx, args.split)
         if args.emul:
@@ -534,6 +536,7 @@ def main() -> int:
     ap.add_argument("--form", default="auto", choices=["auto", "plain", "persist", "tblock", "cluster", "persist_tb"])
     ap.add_argument("--T", type=int, default=0)
     ap.add_argument("--arith", default="exact", choices=["exact", "fma"])
+    ap.add_argument("--layout", type=int, default=-1, help="temporal-blocking register layout (0 strided, 1 contiguous)")
     ap.add_argument("--split", type=int, default=0)
     ap.add_argument("--emul", type=int, default=0)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])

@@ -155,7 +155,8 @@ int heat_set_form(heat_ctx *c, int form, int T);
  * segments.  The result does not depend on this choice. */
 int heat_set_segments(heat_ctx *c, int segments);
 
-/* Binary64 with HEAT_ARITH_EXACT, temporal-blocking form: compute `share` of
+/* Binary64 with HEAT_ARITH_EXACT, temporal-blocking form with the strided
+ * layout (heat_set_layout(c, 0)): compute `share` of
  * every 32 tiles with integer-pipe binary64 arithmetic instead of the FP64 unit
  * (0..32).  GB300's FP64 unit runs at 1/64 of the FP32 rate; the integer pipes
  * are idle during the binary64 update, so splitting the tiles between the two
@@ -165,8 +166,9 @@ int heat_set_segments(heat_ctx *c, int segments);
  * unit. */
 int heat_set_emulation(heat_ctx *c, int share);
 
-/* Binary64 with HEAT_ARITH_EXACT, temporal-blocking form, tiles left on the
- * FP64 unit: move part of each point's update to the integer pipes.  level 0:
+/* Binary64 with HEAT_ARITH_EXACT, temporal-blocking form with the strided
+ * layout, tiles left on the FP64 unit: move part of each point's update to the
+ * integer pipes.  level 0:
  * all four operations (fma for ul - 2u, add, multiply by r, add) on the FP64
  * unit; 1: the multiply by r on the integer pipes (3 FP64 operations per
  * point; for r a power of two the product only moves the exponent); 1 + j

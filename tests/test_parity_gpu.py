@@ -232,3 +232,20 @@ def test_graph_replay_matches_direct_launches(form, T):
         outs.append(h.get())
     for o in outs:
         assert same_bits(o, ref)
+
+
+@pytest.mark.parametrize("form", ["tblock", "cluster", "persist"])
+def test_checkpoint_and_resume_in_a_new_context(form):
+    """heat_get + the step counter is a checkpoint; heat_set in a fresh context
+    resumes it (binary64 runs are split-invariant, so the result is bitwise the
+    uninterrupted run)."""
+    n = 6000
+    u0 = workloads.uniform(n, 77, -1, 1)
+    with H.Heat(n // 4, 4, 0.4, 1.0, 1.0, form=form) as h:
+        h.set(u0).run(13)
+        saved, steps = h.get(), h.steps
+    assert steps == 13
+    with H.Heat(n // 4, 4, 0.4, 1.0, 1.0, form=form) as h2:
+        h2.set(saved).run(30 - steps)
+        resumed = h2.get()
+    assert same_bits(resumed, oracle.run(u0, 0.4, 30))
