@@ -28,6 +28,13 @@
  *     out) are reported by the next synchronising call (heat_sync, heat_get,
  *     heat_sum, heat_get_device).
  *   - A context is not thread-safe: one host thread at a time.
+ *
+ * Citations: the entries that carry the operation (heat_create, heat_set,
+ * heat_run, heat_get and their batch counterparts) implement Section 2 as cited
+ * on each.  The entries that select kernels, tune, observe or test the library
+ * (forms, layouts, graphs, segments, wait limits, fault hooks, info, the
+ * batch runtime's arena and scheduler, the allocation-free stepper) have no
+ * counterpart in the paper and say what they do instead.
  */
 #ifndef HEAT_H
 #define HEAT_H
@@ -70,7 +77,8 @@ typedef enum {
                             swaps ghost values with its neighbours through
                             device-memory flag queues (Section 2's SPSC queues) */
   HEAT_FORM_TBLOCK = 2,  /* temporal blocking: T steps per register-resident tile */
-  HEAT_FORM_AUTO = 3,    /* library picks: HEAT_FORM_CLUSTER for small rings,
+  HEAT_FORM_AUTO = 3,    /* library picks: HEAT_FORM_CLUSTER for every ring the
+                            cluster form takes (measured fastest there),
                             HEAT_FORM_TBLOCK otherwise */
   HEAT_FORM_CLUSTER = 4, /* small rings (up to 16 x 4 windows of output, about
                             31000 binary64 points at T = 8): one thread-block
@@ -127,8 +135,9 @@ int heat_get(heat_ctx *c, double *host_u, int64_t n);
 int heat_set_device(heat_ctx *c, const double *dev_u, int64_t n);
 int heat_get_device(heat_ctx *c, double *dev_u, int64_t n);
 
-/* Advance the state by nt >= 0 steps of Eq. 2 with the current form and
- * arithmetic.  Asynchronous on the context's stream; returns HEAT_EINVAL for
+/* Advance the state by nt >= 0 forward-Euler steps of Eq. 2 (Section 2, with
+ * the periodic boundary u(t, x) = u(t, L + x): the neighbours of point 0 and
+ * N-1 wrap around the ring) with the current form and arithmetic.  Asynchronous on the context's stream; returns HEAT_EINVAL for
  * nt < 0, HEAT_ESTATE if a device error is pending, HEAT_ECUDA if a launch
  * fails.  Errors found on the device during the run surface at the next
  * synchronising call. */
@@ -301,6 +310,18 @@ int heat_batch_autotune(heat_batch *b, int *T_out, int64_t *seg_points_out);
 
 /* Queue subsequent work on cuda_stream (NULL: the batch's own stream). */
 int heat_batch_set_stream(heat_batch *b, void *cuda_stream);
+
+/* Upper bound, in nanoseconds, on a unit's wait for its neighbours' previous
+ * level (default 5e9).  A wait that runs out stops the launch and reports
+ * HEAT_ETIMEOUT at the next heat_batch_sync / heat_batch_get. */
+int heat_batch_set_wait_limit(heat_batch *b, int64_t ns);
+
+/* Test hook (host-side fault injection): in later runs, segment `segment` of
+ * ring `ring_id` stops publishing its completion from level `from_level` on,
+ * so the units that depend on it run out of their bounded waits and the run
+ * ends with HEAT_ETIMEOUT; every kernel returns normally.  A ring id that is
+ * not live (e.g. -1) disables the hook. */
+int heat_batch_inject_stall(heat_batch *b, int32_t ring_id, int64_t segment, int64_t from_level);
 
 /* Cap the batch kernel's CTAs per SM (0: as many as fit).  The launch needs no
  * co-residency, so two batches on two streams with caps that together fit an

@@ -25,7 +25,6 @@ namespace {
 constexpr int64_t kStageElems = int64_t(1) << 22;  // binary64 staging chunk for HEAT_F32C transfers (32 MiB)
 constexpr int kDefaultEmulShare = 0;               // tiles of 32 on the integer pipes by default
 constexpr int kDefaultSplit = 0;                   // per-point FP64/integer split level by default
-constexpr int64_t kClusterAutoPoints = 8192;       // rings up to this size use the cluster form by default
 
 bool is_finite(double x) { return isfinite(x) != 0; }
 
@@ -284,8 +283,10 @@ int heat_run(heat_ctx *c, int64_t nt) {
   // default: one cluster launch for small rings (latency-bound: one launch for
   // all steps, ghost exchange through distributed shared memory), temporal
   // blocking otherwise (the fastest form measured for both dtypes)
-  if (form == HEAT_FORM_AUTO)
-    form = c->geo.N <= kClusterAutoPoints ? HEAT_FORM_CLUSTER : HEAT_FORM_TBLOCK;
+  if (form == HEAT_FORM_AUTO) {
+    const int Tc = c->T > 0 ? c->T : (c->dtype == HEAT_F32C ? 32 : 8);
+    form = c->geo.N <= heat::cluster_max_points(c, Tc) ? HEAT_FORM_CLUSTER : HEAT_FORM_TBLOCK;
+  }
   c->last_form = form;
   c->last_T = 1;
   c->last_launches = 0;

@@ -70,6 +70,9 @@ struct BatchArgs {
   unsigned long long *counter;
   DevStatus *st;
   long long wait_ns;
+  int inj_ring;        // test hook: table index of a ring whose segment stops publishing (-1: none)
+  long long inj_seg;
+  long long inj_level;
 };
 
 __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p) {
@@ -192,7 +195,7 @@ __global__ void __launch_bounds__(kBWarps * 32, MODE == 2 ? 3 : 5) k_batch(Batch
       }
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (threadIdx.x == 0 && !(s_ring == a.inj_ring && s_seg == a.inj_seg && s_level >= a.inj_level)) {
       __threadfence();
       st_release_u32(a.done + R.done_base + s_seg, (unsigned)(s_level + 1));
     }
@@ -265,6 +268,8 @@ struct heat_batch {
   int64_t seg_points = 16384;
   int64_t last_point_steps = 0;
   long long wait_ns = 5000000000LL;
+  int32_t inj_ring_id = -1;  // test hook (heat_batch_inject_stall)
+  int64_t inj_seg = 0, inj_level = 0;
   // saved states (heat_batch_save / heat_batch_restore)
   void *snap = nullptr;
   std::vector<std::pair<int64_t, int>> snap_state;  // per ring id: (done, live)
@@ -431,6 +436,15 @@ int launch_table(heat_batch *b, const Table &t, int T) {
   a.counter = b->d_counter;
   a.st = b->dstat;
   a.wait_ns = b->wait_ns;
+  a.inj_ring = -1;
+  a.inj_seg = 0;
+  a.inj_level = 0;
+  for (size_t i = 0; i < t.ids.size(); ++i)
+    if (t.ids[i] == b->inj_ring_id) {
+      a.inj_ring = (int)i;
+      a.inj_seg = b->inj_seg;
+      a.inj_level = b->inj_level;
+    }
   const int64_t units = t.levp.back();
   const bool f32 = b->dtype == HEAT_F32C;
   const bool fma = !f32 && b->arith == HEAT_ARITH_FMA;
@@ -669,6 +683,20 @@ int heat_batch_set_tuning(heat_batch *b, int T, int64_t seg_points) {
   if (T > 0 && 2 * T >= win) return HEAT_EINVAL;
   if (T > 0) b->T = T;
   if (seg_points > 0) b->seg_points = seg_points;
+  return HEAT_OK;
+}
+
+int heat_batch_set_wait_limit(heat_batch *b, int64_t ns) {
+  if (!b || ns < 1) return HEAT_EINVAL;
+  b->wait_ns = ns;
+  return HEAT_OK;
+}
+
+int heat_batch_inject_stall(heat_batch *b, int32_t ring_id, int64_t segment, int64_t from_level) {
+  if (!b || from_level < 0 || segment < 0) return HEAT_EINVAL;
+  b->inj_ring_id = ring_id;  // a ring id that is not live disables the hook
+  b->inj_seg = segment;
+  b->inj_level = from_level;
   return HEAT_OK;
 }
 

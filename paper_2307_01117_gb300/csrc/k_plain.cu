@@ -54,6 +54,11 @@ __device__ __forceinline__ float f32c_one_step(float hl, float h, float hr, floa
   return f32c_store(hn, ln);
 }
 
+// Binary32 is HBM-bound in this form: a warp first issues the loads of kU
+// consecutive 128-point tiles (kU x 512 bytes in flight per warp), then
+// computes and stores them.
+constexpr int kU = 4;
+
 __global__ void __launch_bounds__(kPlainThreads) k_plain_f32c(const float *__restrict__ u, float *__restrict__ v,
                                                               int64_t N, float rf) {
   const int lane = threadIdx.x & 31;
@@ -61,7 +66,34 @@ __global__ void __launch_bounds__(kPlainThreads) k_plain_f32c(const float *__res
   const int64_t warp = gtid >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const int64_t ntiles = N >> 7;  // 128 points per warp tile (float4 per lane)
-  for (int64_t t = warp; t < ntiles; t += nwarps) {
+  const int64_t ngroups = ntiles / kU;
+  for (int64_t q = warp; q < ngroups; q += nwarps) {
+    const int64_t b0 = q * kU * 128;
+    float4 x[kU];
+#pragma unroll
+    for (int j = 0; j < kU; ++j) x[j] = __ldcs(reinterpret_cast<const float4 *>(u + b0 + 128 * j) + lane);
+    float eleft = 0.0f, eright = 0.0f;
+    if (lane == 0) eleft = u[b0 == 0 ? N - 1 : b0 - 1];
+    if (lane == 31) eright = u[b0 + 128 * kU == N ? 0 : b0 + 128 * kU];
+#pragma unroll
+    for (int j = 0; j < kU; ++j) {
+      float left = __shfl_up_sync(kFull, x[j].w, 1);
+      float right = __shfl_down_sync(kFull, x[j].x, 1);
+      // tile edges: the previous / next tile of the group, or the group's edge loads
+      const float prev_w = __shfl_sync(kFull, x[j > 0 ? j - 1 : 0].w, 31);
+      const float next_x = __shfl_sync(kFull, x[j + 1 < kU ? j + 1 : kU - 1].x, 0);
+      if (lane == 0) left = j > 0 ? prev_w : eleft;
+      if (lane == 31) right = j + 1 < kU ? next_x : eright;
+      float4 y;
+      y.x = f32c_one_step(left, x[j].x, x[j].y, rf);
+      y.y = f32c_one_step(x[j].x, x[j].y, x[j].z, rf);
+      y.z = f32c_one_step(x[j].y, x[j].z, x[j].w, rf);
+      y.w = f32c_one_step(x[j].z, x[j].w, right, rf);
+      __stcs(reinterpret_cast<float4 *>(v + b0 + 128 * j) + lane, y);
+    }
+  }
+  // tiles left over after the groups
+  for (int64_t t = ngroups * kU + warp; t < ntiles; t += nwarps) {
     const int64_t b = t << 7;
     const float4 x = __ldcs(reinterpret_cast<const float4 *>(u + b) + lane);
     float left = __shfl_up_sync(kFull, x.w, 1);
@@ -109,7 +141,7 @@ int run_plain(heat_ctx *c, int64_t nt) {
       else
         k_plain_f64<false><<<grid, kPlainThreads, 0, c->stream>>>((const double *)src, (double *)dst, N, c->r);
     } else {
-      const int grid = plain_grid(c, N >> 7);
+      const int grid = plain_grid(c, (N >> 7) / kU > 0 ? (N >> 7) / kU : 1);
       k_plain_f32c<<<grid, kPlainThreads, 0, c->stream>>>((const float *)src, (float *)dst, N, c->rf);
     }
     const cudaError_t e = cudaGetLastError();

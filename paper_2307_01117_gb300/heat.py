@@ -77,6 +77,8 @@ _PROTOS = {
     "heat_batch_autotune": (_int, [_vp, ctypes.POINTER(_int), ctypes.POINTER(_i64)]),
     "heat_batch_set_stream": (_int, [_vp, _vp]),
     "heat_batch_set_ctas_per_sm": (_int, [_vp, _int]),
+    "heat_batch_set_wait_limit": (_int, [_vp, _i64]),
+    "heat_batch_inject_stall": (_int, [_vp, _i32, _i64, _i64]),
     "heat_batch_save": (_int, [_vp]),
     "heat_batch_restore": (_int, [_vp]),
     "heat_batch_info": (_int, [_vp, ctypes.POINTER(_i32), ctypes.POINTER(_i64), ctypes.POINTER(_i64)]),
@@ -323,6 +325,14 @@ def heat_batch_set_stream(b: int, stream) -> None:
 
 def heat_batch_set_ctas_per_sm(b: int, ctas: int) -> None:
     _check(lib().heat_batch_set_ctas_per_sm(b, int(ctas)), "heat_batch_set_ctas_per_sm")
+
+
+def heat_batch_set_wait_limit(b: int, ns: int) -> None:
+    _check(lib().heat_batch_set_wait_limit(b, int(ns)), "heat_batch_set_wait_limit")
+
+
+def heat_batch_inject_stall(b: int, ring: int, segment: int = 0, from_level: int = 0) -> None:
+    _check(lib().heat_batch_inject_stall(b, int(ring), int(segment), int(from_level)), "heat_batch_inject_stall")
 
 
 def heat_batch_save(b: int) -> None:

@@ -167,3 +167,33 @@ def test_batch_argument_errors():
             H.heat_batch_restore(b)                          # nothing saved yet
     finally:
         H.heat_batch_destroy(b)
+
+
+def test_stalled_segment_times_out_and_batch_recovers():
+    """Host-side fault injection: one segment of one ring stops publishing; the
+    units that wait on it run out of their bounded waits, the run reports
+    HEAT_ETIMEOUT, and after restore (with the hook cleared) the batch runs to
+    the oracle's result."""
+    specs = [(40000, 1, 60, 0.3, workloads.uniform(40000, 1, -1, 1)),
+             (30000, 2, 45, 0.2, workloads.uniform(60000, 2, -1, 1))]
+    b = H.heat_batch_create(sum(nx * np_ + 64 for nx, np_, *_ in specs))
+    try:
+        H.heat_batch_set_tuning(b, 4, 4096)
+        ids = add_all(b, specs)
+        H.heat_batch_save(b)
+        H.heat_batch_set_wait_limit(b, 50_000_000)           # 50 ms
+        H.heat_batch_inject_stall(b, ids[0], 3, 2)
+        H.heat_batch_run(b, 0)
+        with pytest.raises(H.HeatError) as e:
+            H.heat_batch_sync(b)
+        assert e.value.code == H.HEAT_ETIMEOUT
+        with pytest.raises(H.HeatError) as e:
+            H.heat_batch_run(b, 0)
+        assert e.value.code == H.HEAT_ESTATE
+        H.heat_batch_inject_stall(b, -1)
+        H.heat_batch_restore(b)
+        H.heat_batch_run(b, 0)
+        for rid, (nx, np_, nt, k, u0) in zip(ids, specs):
+            assert np.array_equal(bits(H.heat_batch_get(b, rid, nx * np_)), bits(oracle.run(u0, k, nt)))
+    finally:
+        H.heat_batch_destroy(b)

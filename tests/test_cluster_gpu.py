@@ -66,6 +66,9 @@ def test_auto_picks_cluster_for_small_rings():
     with H.Heat(1000, 4, 0.5, 1.0, 1.0) as h:
         h.set(workloads.ramp(4000)).run(10)
         assert H.heat_last_run(h.ctx)["form"] == "cluster"
+    with H.Heat(30000, 1, 0.5, 1.0, 1.0) as h:
+        h.set(np.zeros(30000)).run(10)
+        assert H.heat_last_run(h.ctx)["form"] == "cluster"
     with H.Heat(100000, 1, 0.5, 1.0, 1.0) as h:
         h.set(np.zeros(100000)).run(10)
         assert H.heat_last_run(h.ctx)["form"] == "tblock"
