@@ -17,6 +17,11 @@ namespace {
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kPlainThreads = 256;
 
+// Binary64: a warp takes kU64 consecutive 64-point tiles at a time, so each
+// lane has 2*kU64 independent updates (4 FP64 operations each) to interleave
+// while the FP64 unit drains.
+constexpr int kU64 = 4;
+
 template <bool FMA>
 __global__ void __launch_bounds__(kPlainThreads) k_plain_f64(const double *__restrict__ u, double *__restrict__ v,
                                                              int64_t N, double r) {
@@ -25,7 +30,31 @@ __global__ void __launch_bounds__(kPlainThreads) k_plain_f64(const double *__res
   const int64_t warp = gtid >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const int64_t ntiles = N >> 6;
-  for (int64_t t = warp; t < ntiles; t += nwarps) {
+  const int64_t ngroups = ntiles / kU64;
+  for (int64_t q = warp; q < ngroups; q += nwarps) {
+    const int64_t b0 = q * kU64 * 64;
+    double2 x[kU64];
+#pragma unroll
+    for (int j = 0; j < kU64; ++j) x[j] = __ldcs(reinterpret_cast<const double2 *>(u + b0 + 64 * j) + lane);
+    double eleft = 0.0, eright = 0.0;
+    if (lane == 0) eleft = u[b0 == 0 ? N - 1 : b0 - 1];
+    if (lane == 31) eright = u[b0 + 64 * kU64 == N ? 0 : b0 + 64 * kU64];
+#pragma unroll
+    for (int j = 0; j < kU64; ++j) {
+      double left = __shfl_up_sync(kFull, x[j].y, 1);
+      double right = __shfl_down_sync(kFull, x[j].x, 1);
+      const double prev_y = __shfl_sync(kFull, x[j > 0 ? j - 1 : 0].y, 31);
+      const double next_x = __shfl_sync(kFull, x[j + 1 < kU64 ? j + 1 : kU64 - 1].x, 0);
+      if (lane == 0) left = j > 0 ? prev_y : eleft;
+      if (lane == 31) right = j + 1 < kU64 ? next_x : eright;
+      double2 y;
+      y.x = eq2<FMA>(left, x[j].x, x[j].y, r);
+      y.y = eq2<FMA>(x[j].x, x[j].y, right, r);
+      __stcs(reinterpret_cast<double2 *>(v + b0 + 64 * j) + lane, y);
+    }
+  }
+  // tiles left over after the groups
+  for (int64_t t = ngroups * kU64 + warp; t < ntiles; t += nwarps) {
     const int64_t b = t << 6;
     const double2 x = __ldcs(reinterpret_cast<const double2 *>(u + b) + lane);
     double left = __shfl_up_sync(kFull, x.y, 1);
@@ -135,7 +164,7 @@ int run_plain(heat_ctx *c, int64_t nt) {
     const void *src = c->buf[c->cur];
     void *dst = c->buf[c->cur ^ 1];
     if (c->dtype == HEAT_F64) {
-      const int grid = plain_grid(c, N >> 6);
+      const int grid = plain_grid(c, (N >> 6) / kU64 > 0 ? (N >> 6) / kU64 : 1);
       if (c->arith == HEAT_ARITH_FMA)
         k_plain_f64<true><<<grid, kPlainThreads, 0, c->stream>>>((const double *)src, (double *)dst, N, c->r);
       else

@@ -176,9 +176,9 @@ __global__ void __launch_bounds__(kWarps * 32) k_tblock(TBArgs a) {
 // two shuffles per carried value per lane and step instead of two per point.
 // Windows are loaded and stored with plain indexed accesses (wrapping around the
 // ring's ends where needed); tiles are claimed from the same launch-wide counter.
-template <int MODE>
+template <int MODE, int EP>
 __global__ void __launch_bounds__(kWarps * 32) k_tblock_c(TBArgs a) {
-  using P = TBC<MODE>;
+  using P = TBCx<MODE, EP>;
   using T = typename P::T;
   constexpr int E = P::E;
   constexpr int WIN = 32 * E;
@@ -213,6 +213,46 @@ __global__ void __launch_bounds__(kWarps * 32) k_tblock_c(TBArgs a) {
       const int64_t g = ws + i;
       if (i >= a.T && i < WIN - a.T && g < N) dst[g] = P::store(R, k);
     }
+  }
+}
+
+template <int MODE, int EP>
+int launch_tb_c_ep(heat_ctx *c, TBArgs a) {
+  const int W = 32 * EP - 2 * a.T;
+  a.ntiles = (c->geo.N + W - 1) / W;
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tblock_c<MODE, EP>, kWarps * 32, 0) != cudaSuccess ||
+      per_sm < 1)
+    return HEAT_ECUDA;
+  int64_t grid = (a.ntiles + kWarps - 1) / kWarps;
+  const int64_t cap = (int64_t)per_sm * c->sms;
+  if (grid > cap) grid = cap;
+  if (grid < 1) grid = 1;
+  if (cudaMemsetAsync(c->tile_counter, 0, sizeof(unsigned long long), c->stream) != cudaSuccess) return HEAT_ECUDA;
+  k_tblock_c<MODE, EP><<<(int)grid, kWarps * 32, 0, c->stream>>>(a);
+  return cuda_status(cudaGetLastError());
+}
+
+// Window width for the contiguous layout: the widest window (least halo
+// recomputation) that still gives every SM sub-partition about 16 windows per
+// launch; medium rings get narrower windows so enough warps keep the FP64 unit
+// busy.  A window must leave at least 2T points of output.
+template <int MODE>
+int launch_tb_c(heat_ctx *c, const TBArgs &a) {
+  constexpr int eps[3] = {MODE == 2 ? 8 : 4, MODE == 2 ? 16 : 8, MODE == 2 ? 32 : 16};
+  const int64_t want = 16LL * 4 * c->sms;
+  int pick = 2;
+  while (pick > 0) {
+    const int64_t w = 32LL * eps[pick] - 2 * a.T;
+    if (c->geo.N / w >= want) break;
+    const int64_t w_next = 32LL * eps[pick - 1] - 2 * a.T;
+    if (w_next < 2 * a.T) break;  // the narrower window would be mostly halo
+    --pick;
+  }
+  switch (pick) {
+    case 0: return launch_tb_c_ep<MODE, eps[0]>(c, a);
+    case 1: return launch_tb_c_ep<MODE, eps[1]>(c, a);
+    default: return launch_tb_c_ep<MODE, eps[2]>(c, a);
   }
 }
 
@@ -254,19 +294,7 @@ int launch_tb(heat_ctx *c, const void *src, void *dst, int T, int steps) {
   for (int i = 0; i < 16; ++i)
     if (((i + 1) * j) / 16 > (i * j) / 16) a.add_mask |= 1u << i;
   const size_t smem = smem_bytes<MODE>();
-  if (c->tb_layout == 1) {
-    int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tblock_c<MODE>, kWarps * 32, 0) != cudaSuccess ||
-        per_sm < 1)
-      return HEAT_ECUDA;
-    int64_t grid = (a.ntiles + kWarps - 1) / kWarps;
-    const int64_t cap = (int64_t)per_sm * c->sms;
-    if (grid > cap) grid = cap;
-    if (grid < 1) grid = 1;
-    if (cudaMemsetAsync(c->tile_counter, 0, sizeof(unsigned long long), c->stream) != cudaSuccess) return HEAT_ECUDA;
-    k_tblock_c<MODE><<<(int)grid, kWarps * 32, 0, c->stream>>>(a);
-    return cuda_status(cudaGetLastError());
-  }
+  if (c->tb_layout == 1) return launch_tb_c<MODE>(c, a);
   if (cudaFuncSetAttribute(k_tblock<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
     return HEAT_ECUDA;
   int per_sm = 0;
