@@ -271,7 +271,7 @@ class RingRunner:
             H.heat_set_layout(self.h.ctx, args.layout)
         if args.split:
             H.heat_set_split(self.h.ctx, args.split)
-        if args.emul:
+        if args.emul >= 0:
             H.heat_set_emulation(self.h.ctx, args.emul)
 
     def step(self, ev=None):
@@ -311,6 +311,8 @@ class RingRunner:
         srcs = [f"paper_2307_01117_gb300/csrc/{src}", "paper_2307_01117_gb300/csrc/stencil_ops.cuh"]
         if name in ("k_tblock", "k_cluster", "k_batch"):
             srcs.append("paper_2307_01117_gb300/csrc/tb_core.cuh")
+        if name == "k_tblock":
+            srcs.append("paper_2307_01117_gb300/csrc/dp_emul.cuh")
         steps_per_launch = self.nt / launches
         elem = 8.0 if self.w["dtype"] == "f64" else 4.0
         # every point read once and written once per launch; the persistent form
@@ -327,7 +329,7 @@ class RingRunner:
         w = self.w
         return {"workload": self.args.workload, "nx": w["nx"], "np": w["np"], "N": self.n, "nt": self.nt,
                 "k": w["k"], "dt": w["dt"], "dx": w["dx"], "init": w["init"], "arith": self.args.arith,
-                "split": self.args.split, "emul": self.args.emul,
+                "split": self.args.split, "emul_share_of_32": self.H.heat_get_emulation(self.h.ctx),
                 "l2": "inputs larger than L2 (no flush needed)" if self.n * 8 > 2 * 135e6 else "L2-resident ring"}
 
     def close(self):
@@ -538,7 +540,8 @@ def main() -> int:
     ap.add_argument("--arith", default="exact", choices=["exact", "fma"])
     ap.add_argument("--layout", type=int, default=-1, help="temporal-blocking register layout (0 strided, 1 contiguous)")
     ap.add_argument("--split", type=int, default=0)
-    ap.add_argument("--emul", type=int, default=0)
+    ap.add_argument("--emul", type=int, default=-1,
+                    help="binary64 tiles of 32 on the integer pipes (-1: the library's choice)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")

@@ -164,16 +164,23 @@ int heat_set_form(heat_ctx *c, int form, int T);
  * segments.  The result does not depend on this choice. */
 int heat_set_segments(heat_ctx *c, int segments);
 
-/* Binary64 with HEAT_ARITH_EXACT, temporal-blocking form with the strided
- * layout (heat_set_layout(c, 0)): compute `share` of
- * every 32 tiles with integer-pipe binary64 arithmetic instead of the FP64 unit
- * (0..32).  GB300's FP64 unit runs at 1/64 of the FP32 rate; the integer pipes
- * are idle during the binary64 update, so splitting the tiles between the two
- * raises throughput.  Both paths give the correctly rounded IEEE result, so the
- * state is bitwise the same for every share; points outside the integer
- * routines' domain (subnormal or non-finite values) are recomputed on the FP64
- * unit. */
+/* Binary64 with HEAT_ARITH_EXACT, temporal-blocking form (either layout):
+ * compute `share` of every 32 tiles with integer-pipe binary64 arithmetic
+ * instead of the FP64 unit (0..32), or -1 (the default) to let the library
+ * choose: 3 of 32 with the contiguous layout for rings of at least 64 of the
+ * widest windows per SM (with depth 8 unless heat_set sets one), else 0.
+ * GB300's FP64 unit runs at 1/64 of the FP32 rate; the integer pipes are idle
+ * during the binary64 update, so splitting the tiles between the two raises
+ * throughput.  Both paths give the correctly rounded IEEE result, so the state
+ * is bitwise the same for every share; a tile in which a value leaves the
+ * integer routines' domain (zero, subnormal or non-finite operands or results)
+ * is recomputed on the FP64 unit.  HEAT_EINVAL outside -1..32. */
 int heat_set_emulation(heat_ctx *c, int share);
+
+/* The share of 32 tiles the temporal-blocking form computes on the integer
+ * pipes for this ring as configured now (the automatic choice resolved), into
+ * *share.  HEAT_EINVAL for null arguments. */
+int heat_get_emulation(const heat_ctx *c, int *share);
 
 /* Binary64 with HEAT_ARITH_EXACT, temporal-blocking form with the strided
  * layout, tiles left on the FP64 unit: move part of each point's update to the
@@ -310,6 +317,11 @@ int heat_batch_autotune(heat_batch *b, int *T_out, int64_t *seg_points_out);
 
 /* Queue subsequent work on cuda_stream (NULL: the batch's own stream). */
 int heat_batch_set_stream(heat_batch *b, void *cuda_stream);
+
+/* CUDA graphs for batch runs, on by default: a run's stream operations (table
+ * upload, counter resets, launch) are captured once and replayed while their
+ * shape is unchanged, e.g. for a fixed batch run again after heat_batch_restore. */
+int heat_batch_set_graphs(heat_batch *b, int enable);
 
 /* Upper bound, in nanoseconds, on a unit's wait for its neighbours' previous
  * level (default 5e9).  A wait that runs out stops the launch and reports

@@ -23,7 +23,7 @@ struct NvtxRange {
 namespace {
 
 constexpr int64_t kStageElems = int64_t(1) << 22;  // binary64 staging chunk for HEAT_F32C transfers (32 MiB)
-constexpr int kDefaultEmulShare = 0;               // tiles of 32 on the integer pipes by default
+constexpr int kDefaultEmulShare = -1;              // tiles of 32 on the integer pipes: chosen per ring
 constexpr int kDefaultSplit = 0;                   // per-point FP64/integer split level by default
 
 bool is_finite(double x) { return isfinite(x) != 0; }
@@ -71,12 +71,12 @@ int reset_status(heat_ctx *c) {
 // launches then cost one graph launch instead of one host call each.
 int run_graphed(heat_ctx *c, int form, int64_t nt) {
   const int T = c->T;
-  const int64_t depth = form == HEAT_FORM_PLAIN ? 1 : (T > 0 ? T : (c->dtype == HEAT_F32C ? 32 : 4));
+  const int64_t depth = form == HEAT_FORM_PLAIN ? 1 : (T > 0 ? T : heat::tblock_default_T(c));
   if ((nt + depth - 1) / depth > 8192) return HEAT_ENOTSUP;  // keep graphs small
   const unsigned long long key[8] = {(unsigned long long)form, (unsigned long long)T, (unsigned long long)nt,
                                      (unsigned long long)c->cur, (unsigned long long)c->arith,
                                      (unsigned long long)c->tb_layout,
-                                     ((unsigned long long)c->split_level << 32) | c->emul_mask,
+                                     ((unsigned long long)c->split_level << 32) | heat::tblock_emul_mask(c),
                                      (unsigned long long)(uintptr_t)c->stream};
   if (c->graph_exec && memcmp(key, c->graph_key, sizeof(key)) == 0) {
     if (cudaGraphLaunch(c->graph_exec, c->stream) != cudaSuccess) return HEAT_ECUDA;
@@ -360,13 +360,21 @@ int heat_set_split(heat_ctx *c, int level) {
 }
 
 int heat_set_emulation(heat_ctx *c, int share) {
-  if (!c || share < 0 || share > 32) return HEAT_EINVAL;
+  if (!c || share < -1 || share > 32) return HEAT_EINVAL;
+  c->emul_auto = share < 0;
   c->emul_share = share;
+  if (share < 0) share = 0;
   // spread `share` set bits evenly over 32 positions
   unsigned mask = 0;
   for (int i = 0; i < 32; ++i)
     if (((i + 1) * share) / 32 > (i * share) / 32) mask |= 1u << i;
   c->emul_mask = mask;
+  return HEAT_OK;
+}
+
+int heat_get_emulation(const heat_ctx *c, int *share) {
+  if (!c || !share) return HEAT_EINVAL;
+  *share = __builtin_popcount(heat::tblock_emul_mask(c));
   return HEAT_OK;
 }
 

@@ -73,6 +73,7 @@ struct heat_ctx {
   int64_t last_launches;         // stencil kernel launches queued by the last heat_run
   int emul_share;                // tiles of 32 computed on the integer pipes (binary64, exact reading)
   unsigned emul_mask;            // the same as a bit mask over tile index mod 32
+  int emul_auto;                 // share chosen per ring (heat_set_emulation(c, -1))
   int split_level;               // per-point split of the binary64 update between FP64 unit and integer pipes
   int tb_layout;                 // temporal-blocking register layout: 0 strided (TMA-staged), 1 contiguous
   heat_batch *ptb;               // work-table state of the persistent temporal-blocking form (lazy)
@@ -98,6 +99,8 @@ namespace heat {
 int run_plain(heat_ctx *c, int64_t nt);
 int run_persist(heat_ctx *c, int64_t nt);
 int run_tblock(heat_ctx *c, int64_t nt);
+int tblock_default_T(const heat_ctx *c);
+unsigned tblock_emul_mask(const heat_ctx *c);
 int run_cluster(heat_ctx *c, int64_t nt);
 int run_persist_tb(heat_ctx *c, int64_t nt);
 void free_persist_tb(heat_ctx *c);

@@ -26,6 +26,7 @@
 // with modular indices.  Every point is computed from the same operands as in
 // the single-ring forms, so each ring's result is bitwise its solo result.
 #include <math.h>
+#include <stdint.h>
 #include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
@@ -230,6 +231,12 @@ int per_sm_ctas() {
 
 using heat::BRing;
 
+// What a captured batch run depends on (heat_batch's graph cache).
+struct GraphKey {
+  unsigned long long shape[6];
+  heat::BatchArgs args;
+};
+
 struct heat_batch {
   struct Ring {
     bool live = false;
@@ -269,6 +276,9 @@ struct heat_batch {
   int64_t last_point_steps = 0;
   long long wait_ns = 5000000000LL;
   int32_t inj_ring_id = -1;  // test hook (heat_batch_inject_stall)
+  int graphs = 1;            // capture the run's stream operations and replay them while unchanged
+  cudaGraphExec_t graph_exec = nullptr;
+  GraphKey graph_key = {};
   int64_t inj_seg = 0, inj_level = 0;
   // saved states (heat_batch_save / heat_batch_restore)
   void *snap = nullptr;
@@ -416,14 +426,8 @@ int launch_table(heat_batch *b, const Table &t, int T) {
   memcpy(b->h_stage + o_segp, t.segp.data(), (nr + 1) * sizeof(int64_t));
   memcpy(b->h_stage + o_levp, t.levp.data(), (nl + 1) * sizeof(int64_t));
   memcpy(b->h_stage + o_act, t.active.data(), nl * sizeof(int32_t));
-  if (cudaMemcpyAsync(b->d_blob, b->h_stage, bytes, cudaMemcpyHostToDevice, b->stream) != cudaSuccess)
-    return HEAT_ECUDA;
-  if (cudaEventRecord(b->staged, b->stream) != cudaSuccess) return HEAT_ECUDA;
-  b->staged_pending = true;
-  if (cudaMemsetAsync(b->d_done, 0, ndone * sizeof(unsigned), b->stream) != cudaSuccess) return HEAT_ECUDA;
-  if (cudaMemsetAsync(b->d_counter, 0, sizeof(unsigned long long), b->stream) != cudaSuccess) return HEAT_ECUDA;
-
   heat::BatchArgs a;
+  memset(&a, 0, sizeof(a));  // padding too: the graph key hashes the bytes
   a.arena0 = b->arena[0];
   a.arena1 = b->arena[1];
   a.rings = (const BRing *)(b->d_blob + o_rings);
@@ -453,10 +457,68 @@ int launch_table(heat_batch *b, const Table &t, int T) {
   if (b->ctas_per_sm > 0 && b->ctas_per_sm < per_sm) per_sm = b->ctas_per_sm;
   const int resident = per_sm * b->sms;
   const int grid = (int)std::min<int64_t>(resident, units);
-  const cudaError_t e = f32   ? heat::launch_batch<2>(a, grid, b->stream)
-                        : fma ? heat::launch_batch<1>(a, grid, b->stream)
-                              : heat::launch_batch<0>(a, grid, b->stream);
-  return e == cudaSuccess ? HEAT_OK : HEAT_ECUDA;
+  // The run is four stream operations: the table upload (from the pinned
+  // staging buffer), two counter resets and the launch.  They are captured
+  // into a CUDA graph and replayed while their shape -- byte counts, grid,
+  // kernel arguments -- is unchanged (a fixed batch run again, e.g. after
+  // heat_batch_restore); the upload node copies whatever the staging buffer
+  // holds when the graph runs, so the table contents may differ.
+  auto enqueue = [&](bool capturing) -> cudaError_t {
+    cudaError_t e = cudaMemcpyAsync(b->d_blob, b->h_stage, bytes, cudaMemcpyHostToDevice, b->stream);
+    // the staging buffer may be refilled as soon as its copy is done; inside a
+    // capture the record becomes an event-record node of the graph, so every
+    // replay records `staged` too
+    if (e == cudaSuccess)
+      e = cudaEventRecordWithFlags(b->staged, b->stream, capturing ? cudaEventRecordExternal : cudaEventRecordDefault);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_done, 0, ndone * sizeof(unsigned), b->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_counter, 0, sizeof(unsigned long long), b->stream);
+    if (e == cudaSuccess)
+      e = f32 ? heat::launch_batch<2>(a, grid, b->stream)
+              : fma ? heat::launch_batch<1>(a, grid, b->stream) : heat::launch_batch<0>(a, grid, b->stream);
+    return e;
+  };
+  // the run's shape: operation sizes, grid, kernel, stream, staging buffer and
+  // the kernel arguments byte for byte
+  GraphKey key;
+  memset(&key, 0, sizeof(key));
+  key.shape[0] = bytes;
+  key.shape[1] = ndone;
+  key.shape[2] = (unsigned long long)grid;
+  key.shape[3] = (unsigned long long)(f32 ? 2 : fma ? 1 : 0);
+  key.shape[4] = (unsigned long long)(uintptr_t)b->stream;
+  key.shape[5] = (unsigned long long)(uintptr_t)b->h_stage;
+  memcpy(&key.args, &a, sizeof(a));
+  cudaError_t e = cudaSuccess;
+  if (b->graphs && b->graph_exec && memcmp(&key, &b->graph_key, sizeof(key)) == 0) {
+    e = cudaGraphLaunch(b->graph_exec, b->stream);
+  } else if (b->graphs) {
+    if (b->graph_exec) {
+      cudaGraphExecDestroy(b->graph_exec);
+      b->graph_exec = nullptr;
+    }
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t ex = nullptr;
+    bool captured = false;
+    if (cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+      const cudaError_t ee = enqueue(true);
+      const cudaError_t ec = cudaStreamEndCapture(b->stream, &g);
+      captured = ee == cudaSuccess && ec == cudaSuccess && g && cudaGraphInstantiate(&ex, g, 0) == cudaSuccess;
+      if (g) cudaGraphDestroy(g);
+    }
+    cudaGetLastError();
+    if (captured) {
+      b->graph_exec = ex;
+      memcpy(&b->graph_key, &key, sizeof(key));
+      e = cudaGraphLaunch(ex, b->stream);
+    } else {
+      e = enqueue(false);  // not capturable here: plain stream operations
+    }
+  } else {
+    e = enqueue(false);
+  }
+  if (e != cudaSuccess) return HEAT_ECUDA;
+  b->staged_pending = true;
+  return HEAT_OK;
 }
 
 void free_batch(heat_batch *b) {
@@ -472,6 +534,7 @@ void free_batch(heat_batch *b) {
   if (b->h_stage) cudaFreeHost(b->h_stage);
   if (b->staged) cudaEventDestroy(b->staged);
   if (b->snap) cudaFree(b->snap);
+  if (b->graph_exec) cudaGraphExecDestroy(b->graph_exec);
   if (b->own_stream) cudaStreamDestroy(b->own_stream);
   delete b;
 }
@@ -683,6 +746,12 @@ int heat_batch_set_tuning(heat_batch *b, int T, int64_t seg_points) {
   if (T > 0 && 2 * T >= win) return HEAT_EINVAL;
   if (T > 0) b->T = T;
   if (seg_points > 0) b->seg_points = seg_points;
+  return HEAT_OK;
+}
+
+int heat_batch_set_graphs(heat_batch *b, int enable) {
+  if (!b) return HEAT_EINVAL;
+  b->graphs = enable ? 1 : 0;
   return HEAT_OK;
 }
 
@@ -936,6 +1005,7 @@ void free_persist_tb(heat_ctx *c) {
   if (b->d_counter) cudaFree(b->d_counter);
   if (b->h_stage) cudaFreeHost(b->h_stage);
   if (b->staged) cudaEventDestroy(b->staged);
+  if (b->graph_exec) cudaGraphExecDestroy(b->graph_exec);
   delete b;
   c->ptb = nullptr;
 }

@@ -206,7 +206,29 @@ __global__ void __launch_bounds__(kWarps * 32) k_tblock_c(TBArgs a) {
         P::load(R, k, src[g]);
       }
     }
-    for (int s = 0; s < a.steps; ++s) P::step(R, lane, a.r, a.rf);
+    bool dp = true;
+    if constexpr (MODE == 0) {
+      if ((a.emul_mask >> (unsigned)(tile & 31)) & 1u) {  // this tile on the integer pipes
+        bool bad = false;
+        for (int s = 0; s < a.steps; ++s) P::step_emul(R, a.m, bad);
+        dp = __any_sync(kFull, bad);
+        if (dp) {  // a value left the routines' domain: reload and redo on the FP64 unit
+          if (ws >= 0 && ws + WIN <= N) {
+#pragma unroll
+            for (int k = 0; k < E; ++k) P::load(R, k, src[base + k]);
+          } else {
+#pragma unroll
+            for (int k = 0; k < E; ++k) {
+              int64_t g = (base + k) % N;
+              if (g < 0) g += N;
+              P::load(R, k, src[g]);
+            }
+          }
+        }
+      }
+    }
+    if (dp)
+      for (int s = 0; s < a.steps; ++s) P::step(R, lane, a.r, a.rf);
 #pragma unroll
     for (int k = 0; k < E; ++k) {
       const int i = E * lane + k;
@@ -281,7 +303,7 @@ int launch_tb(heat_ctx *c, const void *src, void *dst, int T, int steps) {
   memcpy(&rbits, &c->r, sizeof(rbits));
   const int rexp = (int)((rbits >> 52) & 2047);
   // the routines take a normal, nonzero multiplier; otherwise every tile uses the FP64 unit
-  a.emul_mask = (MODE == 0 && rexp >= 1 && rexp <= 2046) ? c->emul_mask : 0u;
+  a.emul_mask = (MODE == 0 && rexp >= 1 && rexp <= 2046) ? tblock_emul_mask(c) : 0u;
   a.m = emul::prepare_mul(rbits);
   a.tile_counter = c->tile_counter;
   // split_level 0: every FP64-unit tile keeps 4 FP64 operations per point;
@@ -314,9 +336,28 @@ int launch_tb(heat_ctx *c, const void *src, void *dst, int T, int steps) {
 
 int tblock_window(int dtype) { return dtype == HEAT_F32C ? 32 * TB<2>::E : 32 * TB<0>::E; }
 
+// The automatic integer-pipe share: 3 of every 32 tiles, for binary64 rings
+// under the exact reading in the contiguous layout that give every SM at least
+// 64 of the widest windows (smaller rings finish in a few waves of tiles, where
+// the slower integer tiles would only lengthen the last wave).
+unsigned tblock_emul_mask(const heat_ctx *c) {
+  if (!c->emul_auto) return c->emul_mask;
+  if (c->dtype != HEAT_F64 || c->arith != HEAT_ARITH_EXACT || c->tb_layout != 1) return 0u;
+  if (c->geo.N < 64LL * c->sms * (32 * 16 - 2 * 8)) return 0u;
+  return (1u << 10) | (1u << 21) | (1u << 31);  // share 3, spread evenly
+}
+
+// Default depth: binary32 pairs 32 steps per pass; binary64 4, or 8 when part of
+// the tiles run on the integer pipes (their share of the work grows with T,
+// while the FP64 tiles' halo cost grows too; 8 measured best with share 3).
+int tblock_default_T(const heat_ctx *c) {
+  if (c->dtype == HEAT_F32C) return 32;
+  return tblock_emul_mask(c) ? 8 : 4;
+}
+
 int run_tblock(heat_ctx *c, int64_t nt) {
   const int mode = c->dtype == HEAT_F32C ? 2 : (c->arith == HEAT_ARITH_FMA ? 1 : 0);
-  int T = c->T > 0 ? c->T : (c->dtype == HEAT_F32C ? 32 : 4);
+  int T = c->T > 0 ? c->T : tblock_default_T(c);
   const int WIN = tblock_window(c->dtype);
   if (2 * T >= WIN) return HEAT_EINVAL;
   c->last_T = T;

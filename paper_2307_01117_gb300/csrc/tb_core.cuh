@@ -198,7 +198,26 @@ struct TBCf64 {
   }
 };
 template <int EP>
-struct TBCx<0, EP> : TBCf64<0, EP> {};
+struct TBCx<0, EP> : TBCf64<0, EP> {
+  // The step with the integer-pipe binary64 routines (dp_emul.cuh); `bad` is
+  // set when a value leaves their domain and the caller redoes the tile on the
+  // FP64 unit.
+  static __device__ __forceinline__ void step_emul(typename TBCf64<0, EP>::Reg &R, const emul::Mul &m, bool &bad) {
+    constexpr int E = EP;
+    const double left = __shfl_up_sync(kFull, R.x[E - 1], 1);
+    const double right = __shfl_down_sync(kFull, R.x[0], 1);
+    uint64_t prev = (uint64_t)__double_as_longlong(left);
+    uint64_t cur = (uint64_t)__double_as_longlong(R.x[0]);
+#pragma unroll
+    for (int k = 0; k < E; ++k) {
+      const uint64_t nxt = (uint64_t)__double_as_longlong(k + 1 < E ? R.x[k + 1] : right);
+      const uint64_t v = emul::eq2_exact(prev, cur, nxt, m, bad);
+      prev = cur;
+      cur = nxt;
+      R.x[k] = __longlong_as_double((long long)v);
+    }
+  }
+};
 template <int EP>
 struct TBCx<1, EP> : TBCf64<1, EP> {};
 

@@ -52,6 +52,7 @@ _PROTOS = {
     "heat_set_arith": (_int, [_vp, _int]),
     "heat_set_segments": (_int, [_vp, _int]),
     "heat_set_emulation": (_int, [_vp, _int]),
+    "heat_get_emulation": (_int, [_vp, ctypes.POINTER(ctypes.c_int)]),
     "heat_set_split": (_int, [_vp, _int]),
     "heat_set_layout": (_int, [_vp, _int]),
     "heat_set_graphs": (_int, [_vp, _int]),
@@ -78,6 +79,7 @@ _PROTOS = {
     "heat_batch_set_stream": (_int, [_vp, _vp]),
     "heat_batch_set_ctas_per_sm": (_int, [_vp, _int]),
     "heat_batch_set_wait_limit": (_int, [_vp, _i64]),
+    "heat_batch_set_graphs": (_int, [_vp, _int]),
     "heat_batch_inject_stall": (_int, [_vp, _i32, _i64, _i64]),
     "heat_batch_save": (_int, [_vp]),
     "heat_batch_restore": (_int, [_vp]),
@@ -185,6 +187,12 @@ def heat_set_segments(ctx: int, segments: int) -> None:
 
 def heat_set_emulation(ctx: int, share: int) -> None:
     _check(lib().heat_set_emulation(ctx, int(share)), "heat_set_emulation")
+
+
+def heat_get_emulation(ctx: int) -> int:
+    share = ctypes.c_int(0)
+    _check(lib().heat_get_emulation(ctx, ctypes.byref(share)), "heat_get_emulation")
+    return share.value
 
 
 def heat_set_graphs(ctx: int, enable: bool) -> None:
@@ -325,6 +333,10 @@ def heat_batch_set_stream(b: int, stream) -> None:
 
 def heat_batch_set_ctas_per_sm(b: int, ctas: int) -> None:
     _check(lib().heat_batch_set_ctas_per_sm(b, int(ctas)), "heat_batch_set_ctas_per_sm")
+
+
+def heat_batch_set_graphs(b: int, enable: bool) -> None:
+    _check(lib().heat_batch_set_graphs(b, int(bool(enable))), "heat_batch_set_graphs")
 
 
 def heat_batch_set_wait_limit(b: int, ns: int) -> None:

@@ -197,3 +197,21 @@ def test_stalled_segment_times_out_and_batch_recovers():
             assert np.array_equal(bits(H.heat_batch_get(b, rid, nx * np_)), bits(oracle.run(u0, k, nt)))
     finally:
         H.heat_batch_destroy(b)
+
+
+def test_graph_replay_of_a_fixed_batch():
+    """Restore + run of the same batch replays the captured graph; results stay
+    the oracle's, with graphs on and off."""
+    specs = small_table(12, seed=51, nt_hi=150)
+    b = H.heat_batch_create(sum(nx * np_ + 64 for nx, np_, *_ in specs))
+    try:
+        ids = add_all(b, specs)
+        H.heat_batch_save(b)
+        for graphs in (True, True, True, False):
+            H.heat_batch_set_graphs(b, graphs)
+            H.heat_batch_restore(b)
+            H.heat_batch_run(b, 0)
+            for rid, (nx, np_, nt, k, u0) in zip(ids, specs):
+                assert np.array_equal(bits(H.heat_batch_get(b, rid, nx * np_)), bits(oracle.run(u0, k, nt)))
+    finally:
+        H.heat_batch_destroy(b)

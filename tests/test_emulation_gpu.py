@@ -17,8 +17,9 @@ def built():
     build.build()
 
 
-def run(u0, r, nt, T, share):
+def run(u0, r, nt, T, share, layout=1):
     with H.Heat(len(u0), 1, r, 1.0, 1.0, form="tblock", T=T) as h:
+        H.heat_set_layout(h.ctx, layout)
         H.heat_set_emulation(h.ctx, share)
         h.set(u0).run(nt)
         return h.get()
@@ -28,13 +29,14 @@ def bits(a):
     return np.asarray(a).view(np.uint64)
 
 
+@pytest.mark.parametrize("layout", [0, 1])
 @pytest.mark.parametrize("share", [0, 1, 8, 16, 31, 32])
 @pytest.mark.parametrize("r", [0.25, 0.5, 0.3, 0.123456789])
-def test_every_share_is_bitwise_the_oracle(share, r):
+def test_every_share_is_bitwise_the_oracle(share, r, layout):
     n = 3 * 4096 + 17
     u0 = workloads.uniform(n, 90 + share, -1, 1)
     ref = oracle.run(u0, r, 21)
-    assert np.array_equal(bits(run(u0, r, 21, 7, share)), bits(ref))
+    assert np.array_equal(bits(run(u0, r, 21, 7, share, layout)), bits(ref))
 
 
 @pytest.mark.parametrize("share", [16, 32])
@@ -44,8 +46,9 @@ def test_paper_ramp_with_zero_second_differences(share):
     assert np.array_equal(bits(run(u0, 0.5, 100, 4, share)), bits(ref))
 
 
+@pytest.mark.parametrize("layout", [0, 1])
 @pytest.mark.parametrize("share", [32])
-def test_out_of_domain_values_fall_back(share):
+def test_out_of_domain_values_fall_back(share, layout):
     n = 8192
     u0 = workloads.uniform(n, 3, -1, 1)
     u0[100:140] = 0.0
@@ -53,7 +56,7 @@ def test_out_of_domain_values_fall_back(share):
     u0[900] = -0.0
     u0[2000:2010] = 1e-300         # results go subnormal after a few steps
     ref = oracle.run(u0, 0.37, 12)
-    assert np.array_equal(bits(run(u0, 0.37, 12, 4, share)), bits(ref))
+    assert np.array_equal(bits(run(u0, 0.37, 12, 4, share, layout)), bits(ref))
 
 
 def test_constant_field_stays_constant():
@@ -67,6 +70,7 @@ def test_split_levels_are_bitwise_the_oracle(split, r):
     n = 2 * 4096 + 333
     u0 = workloads.uniform(n, 7 + split, -1, 1)
     with H.Heat(n, 1, r, 1.0, 1.0, form="tblock", T=5) as h:
+        H.heat_set_layout(h.ctx, 0)                 # the split applies to the strided layout
         H.heat_set_split(h.ctx, split)
         h.set(u0).run(23)
         got = h.get()
@@ -79,7 +83,30 @@ def test_split_with_out_of_domain_values():
     u0[10:30] = 0.0
     u0[300:310] = 4e-310
     with H.Heat(n, 1, 0.3, 1.0, 1.0, form="tblock", T=4) as h:
+        H.heat_set_layout(h.ctx, 0)
         H.heat_set_split(h.ctx, 17)
         h.set(u0).run(10)
         got = h.get()
     assert np.array_equal(bits(got), bits(oracle.run(u0, 0.3, 10)))
+
+
+def test_automatic_share_is_resolved_per_ring_and_exact():
+    """The default (-1): large binary64 rings put 3 of 32 tiles on the integer
+    pipes at depth 8; small rings keep every tile on the FP64 unit."""
+    n = 5_000_000                                   # above 64 windows of 496 points per SM
+    u0 = workloads.uniform_plus_mode(n, seed=5, m=3)
+    with H.Heat(n // 4, 4, 0.25, 1.0, 1.0, form="tblock") as h:
+        assert H.heat_get_emulation(h.ctx) == 3
+        h.set(u0).run(20)
+        assert H.heat_last_run(h.ctx)["T"] == 8
+        got = h.get()
+        H.heat_set_emulation(h.ctx, 0)
+        assert H.heat_get_emulation(h.ctx) == 0
+    assert np.array_equal(bits(got), bits(oracle.run(u0, 0.25, 20)))
+    with H.Heat(40000, 1, 0.25, 1.0, 1.0, form="tblock") as h:
+        assert H.heat_get_emulation(h.ctx) == 0
+        h.set(workloads.uniform(40000, 6, -1, 1)).run(9)
+        assert H.heat_last_run(h.ctx)["T"] == 4
+    with pytest.raises(H.HeatError):
+        with H.Heat(100, 1, 0.25, 1.0, 1.0) as h:
+            H.heat_set_emulation(h.ctx, -2)
