@@ -167,14 +167,18 @@ int heat_set_segments(heat_ctx *c, int segments);
 /* Binary64 with HEAT_ARITH_EXACT, temporal-blocking form (either layout):
  * compute `share` of every 32 tiles with integer-pipe binary64 arithmetic
  * instead of the FP64 unit (0..32), or -1 (the default) to let the library
- * choose: 3 of 32 with the contiguous layout for rings of at least 64 of the
- * widest windows per SM (with depth 8 unless heat_set sets one), else 0.
+ * choose: 16 of 32 with the contiguous layout for rings of at least 64 of the
+ * widest windows per SM (with depth 8 unless heat_set_form sets one), else 0.
  * GB300's FP64 unit runs at 1/64 of the FP32 rate; the integer pipes are idle
  * during the binary64 update, so splitting the tiles between the two raises
  * throughput.  Both paths give the correctly rounded IEEE result, so the state
- * is bitwise the same for every share; a tile in which a value leaves the
- * integer routines' domain (zero, subnormal or non-finite operands or results)
- * is recomputed on the FP64 unit.  HEAT_EINVAL outside -1..32. */
+ * is bitwise the same for every share.  Strided layout: a tile in which a
+ * value leaves the integer routines' domain (subnormal or non-finite operands or
+ * results, signed zeros) is recomputed on the FP64 unit.  Contiguous layout: a
+ * tile runs on the integer pipes only if its values pass a screen (+0, or
+ * normal magnitudes within bounds derived from T and r that keep every
+ * intermediate result normal), else on the FP64 unit.  HEAT_EINVAL outside
+ * -1..32. */
 int heat_set_emulation(heat_ctx *c, int share);
 
 /* The share of 32 tiles the temporal-blocking form computes on the integer
@@ -322,6 +326,13 @@ int heat_batch_set_stream(heat_batch *b, void *cuda_stream);
  * upload, counter resets, launch) are captured once and replayed while their
  * shape is unchanged, e.g. for a fixed batch run again after heat_batch_restore. */
 int heat_batch_set_graphs(heat_batch *b, int enable);
+
+/* Binary64 batches (exact reading): `share` of every 32 tiles of each work unit
+ * computed on the integer pipes instead of the FP64 unit (0..32), or -1 (the
+ * default) for the library's choice, 16.  A tile runs there only if its values
+ * pass the screen described at heat_set_emulation; the state is bitwise the
+ * same for every share.  HEAT_EINVAL outside -1..32. */
+int heat_batch_set_emulation(heat_batch *b, int share);
 
 /* Upper bound, in nanoseconds, on a unit's wait for its neighbours' previous
  * level (default 5e9).  A wait that runs out stops the launch and reports

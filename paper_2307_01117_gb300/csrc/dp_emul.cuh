@@ -166,5 +166,149 @@ HEAT_HD uint64_t eq2_exact(uint64_t ul, uint64_t u, uint64_t ur, const Mul &m, b
   return add(u, t3, bad);
 }
 
+// ---------------------------------------------------------------------------
+// Unpacked form, for whole temporal-blocking tiles on the integer pipes.
+//
+// A value is held as x = m * 2^e with m a signed (two's complement) 64-bit
+// integer, 2^52 <= |m| <= 2^53, or m = 0 (x = +0) with e very negative.  A
+// tile's values are unpacked once, advanced T steps without packing, and
+// packed once.  The tile's inputs are screened first (in_domain): zero or a
+// normal magnitude within [2^(lo-1023), 2^(hi-1022)), bounds the host derives
+// from T and r so that every intermediate result of the T steps is +0 or a
+// normal, finite binary64 number (no -0: it cannot arise from such inputs).
+// Under that guarantee add/mul/eq2 below are the correctly rounded binary64
+// operations without any range test.
+struct X {
+  int64_t m;
+  int32_t e;
+  int32_t pad;
+};
+
+constexpr int32_t kZeroE = -(1 << 24);  // exponent of +0: below every other
+
+HEAT_HD X unpack(uint64_t b) {  // b: +0 or normal
+  const int be = (int)(b >> 52) & 2047;
+  const int64_t mag = (int64_t)((b & kFrac) | kImpl);
+  X x;
+  x.m = be ? ((b >> 63) ? -mag : mag) : 0;
+  x.e = be ? be - 1075 : kZeroE;
+  x.pad = 0;
+  return x;
+}
+
+HEAT_HD uint64_t pack(X x) {
+  const uint64_t mag = (uint64_t)(x.m < 0 ? -x.m : x.m);
+  // biased exponent e + 1075 for |m| in [2^52, 2^53); |m| = 2^53 carries into it
+  const uint64_t v = ((uint64_t)(x.e + 1074) << 52) + mag;
+  return x.m ? (((uint64_t)x.m & kSign) | v) : 0ull;
+}
+
+// Screen: +0, or a normal value with biased exponent in [lo, hi].
+HEAT_HD bool in_domain(uint64_t b, int lo, int hi) {
+  const int be = (int)(b >> 52) & 2047;
+  return b == 0 || (be >= lo && be <= hi);
+}
+
+// x + y, rounded to nearest-even.  The larger-exponent operand is scaled by 2^7
+// (|A| <= 2^60), the other aligned to it by an arithmetic right shift whose lost
+// bits are kept as a sticky 1 in bit 0; the sum (|S| <= 2^61) is shifted left
+// until its leading bit (of |S|, found on the one's complement) sits at bit 61
+// and rounded at bit 9 by floor((S + 255 + bit9) / 2^9), which is round to
+// nearest-even for two's complement values too.  A negative power of two
+// normalises one place high and rounds exactly to |m| = 2^53.
+HEAT_HD X add(X x, X y) {
+  const int d = x.e - y.e;
+  const bool sw = d < 0;
+  const int64_t mb = sw ? y.m : x.m;
+  const int64_t ms = sw ? x.m : y.m;
+  const int eb = sw ? y.e : x.e;
+  int sh = sw ? -d : d;
+  sh = sh < 63 ? sh : 63;
+  const int64_t A = (int64_t)((uint64_t)mb << 7);
+  const int64_t Bs = (int64_t)((uint64_t)ms << 7);
+  int64_t B = Bs >> sh;
+  B |= (int64_t)(((uint64_t)B << sh) != (uint64_t)Bs);  // sticky
+  const int64_t S = A + B;
+  const int lz = clz64((uint64_t)(S ^ (S >> 63)));      // 2 .. 64 (64: S = 0)
+  const int64_t Sn = (int64_t)((uint64_t)S << (lz - 2));
+  X r;
+  r.m = (Sn + 255 + ((Sn >> 9) & 1)) >> 9;
+  r.e = S ? eb + 4 - lz : kZeroE;
+  r.pad = 0;
+  return r;
+}
+
+// A multiplier r (normal, nonzero) prepared for the unpacked form.
+struct MulX {
+  uint64_t sig11;  // significand with its leading 1 at bit 63
+  int e;           // r = sig * 2^e with sig in [2^52, 2^53)
+  bool neg;
+  bool pow2;       // r = +-2^k: the product only moves the exponent
+};
+
+HEAT_HD MulX prepare_mulx(uint64_t r) {
+  MulX m;
+  m.sig11 = ((r & kFrac) | kImpl) << 11;
+  m.e = (int)((r & kAbs) >> 52) - 1075;
+  m.neg = (r >> 63) != 0;
+  m.pow2 = (r & kFrac) == 0;
+  return m;
+}
+
+// r * x for r = +-2^k.
+HEAT_HD X scale(X x, const MulX &r) {
+  X y;
+  y.m = r.neg ? -x.m : x.m;
+  y.e = x.e + r.e + 52;
+  y.pad = 0;
+  return y;
+}
+
+// r * x, rounded to nearest-even: |m| * 2^10 times r's significand * 2^11 is a
+// 128-bit product in [2^125, 2^127); its high word, normalised to a leading 1 at
+// bit 62 with the remaining bits as a sticky bit, is rounded at bit 10.
+HEAT_HD X mul(X x, const MulX &r) {
+  const bool xn = x.m < 0;
+  const uint64_t a = (uint64_t)(xn ? -x.m : x.m) << 10;
+  const uint64_t hi = mulhi64(a, r.sig11);
+  const uint64_t lo = a * r.sig11;
+  const int top = (int)(hi >> 62);  // 1: leading 1 at bit 62; 0: at bit 61 (or x = 0)
+  uint64_t s = top ? hi : ((hi << 1) | (lo >> 63));
+  const uint64_t rest = top ? lo : (lo << 1);
+  s |= (uint64_t)(rest != 0);
+  const uint64_t q = (s + 511 + ((s >> 10) & 1)) >> 10;
+  X y;
+  y.m = (xn != r.neg) ? -(int64_t)q : (int64_t)q;
+  y.e = x.e + r.e + 52 + top;
+  y.pad = 0;
+  return y;
+}
+
+// Eq. 2, exact reading, unpacked: u + r*((ul - 2u) + ur), each step rounded.
+template <bool POW2>
+HEAT_HD X eq2x(X ul, X u, X ur, const MulX &r) {
+  X m2u;
+  m2u.m = -u.m;  // -2u, exact
+  m2u.e = u.e + 1;
+  m2u.pad = 0;
+  const X t2 = add(add(ul, m2u), ur);
+  return add(u, POW2 ? scale(t2, r) : mul(t2, r));
+}
+
+// Screening bounds for T steps with multiplier r (normal, nonzero); false when
+// no input passes.  Every value the steps produce is an integer multiple of
+// the inputs' granularity g = 2^(emin - 52), shrunk by at most 2^(52 - e_r)
+// per step through the product, so a nonzero result is at least
+// g * 2^(-T (52 - e_r)); magnitudes grow at most by (1 + 4|r|) per step.
+HEAT_HD bool domain_bounds(uint64_t r, int T, int &lo, int &hi) {
+  const int er = (int)((r & kAbs) >> 52) - 1023;  // |r| in [2^er, 2^(er+1))
+  const int shrink = er < 52 ? 52 - er : 0;
+  lo = 53 + T * shrink + 3;
+  // ceil(log2(1 + 4|r|)) <= max(er + 3, 0) + 1
+  const int grow = (er + 3 > 0 ? er + 3 : 0) + 1;
+  hi = 2040 - T * (grow + 1) - (er > 0 ? er + 1 : 0);
+  return lo <= hi;
+}
+
 }  // namespace emul
 }  // namespace heat

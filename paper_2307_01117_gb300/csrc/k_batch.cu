@@ -56,6 +56,8 @@ struct BRing {
   double r;
   float rf;
   int parity;         // arena buffer holding the state at the start of the run
+  emul::MulX mx;      // r for the integer-pipe tiles (binary64, exact reading)
+  int dom_lo, dom_hi; // their input screen for T steps (empty: dom_lo > dom_hi)
 };
 
 struct BatchArgs {
@@ -67,6 +69,7 @@ struct BatchArgs {
   const int32_t *active;  // rings active at each level (L)
   int L;
   int T;
+  unsigned emul_mask;  // bit (tile mod 32) set: that tile of a unit on the integer pipes
   unsigned *done;
   unsigned long long *counter;
   DevStatus *st;
@@ -129,6 +132,7 @@ __global__ void __launch_bounds__(kBWarps * 32, MODE == 2 ? 3 : 5) k_batch(Batch
   constexpr int WIN = 32 * E;
   __shared__ long long s_ring, s_level, s_lo, s_hi, s_steps, s_seg;
   __shared__ int s_stop;
+  __shared__ int s_tile;  // the unit's tiles are claimed by the CTA's warps in order
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
   const int64_t total = a.levp[a.L];
@@ -163,6 +167,7 @@ __global__ void __launch_bounds__(kBWarps * 32, MODE == 2 ? 3 : 5) k_batch(Batch
         s_steps = left < a.T ? left : a.T;
       }
       s_stop = stop;
+      s_tile = 0;
     }
     __syncthreads();
     if (s_stop) break;  // uniform across the CTA
@@ -173,7 +178,11 @@ __global__ void __launch_bounds__(kBWarps * 32, MODE == 2 ? 3 : 5) k_batch(Batch
     const int64_t lo = s_lo, hi = s_hi, n = R.n;
     const int steps = (int)s_steps;
     const int64_t ntile = (hi - lo + W - 1) / W;
-    for (int64_t t = wib; t < ntile; t += kBWarps) {
+    for (;;) {
+      int tc = 0;
+      if (lane == 0) tc = atomicAdd(&s_tile, 1);
+      const int64_t t = __shfl_sync(0xffffffffu, tc, 0);
+      if (t >= ntile) break;
       const int64_t ws = lo + t * W - a.T;
       typename P::Reg reg;
       const bool inside = ws >= 0 && ws + WIN <= n;
@@ -186,7 +195,24 @@ __global__ void __launch_bounds__(kBWarps * 32, MODE == 2 ? 3 : 5) k_batch(Batch
         }
         P::load(reg, k, __ldcg(src + g));
       }
-      for (int s = 0; s < steps; ++s) P::step(reg, lane, R.r, R.rf);
+      bool dp = true;
+      if constexpr (MODE == 0) {
+        if ((a.emul_mask >> (unsigned)(t & 31)) & 1u) {  // this tile on the integer pipes
+          bool ok = true;
+#pragma unroll
+          for (int k = 0; k < E; ++k)
+            ok &= emul::in_domain((uint64_t)__double_as_longlong(P::store(reg, k)), R.dom_lo, R.dom_hi);
+          if (__all_sync(0xffffffffu, ok)) {
+            if (R.mx.pow2)
+              P::template steps_x<true>(reg, steps, R.mx);
+            else
+              P::template steps_x<false>(reg, steps, R.mx);
+            dp = false;
+          }
+        }
+      }
+      if (dp)
+        for (int s = 0; s < steps; ++s) P::step(reg, lane, R.r, R.rf);
       const int64_t out_hi = lo + (t + 1) * W < hi ? lo + (t + 1) * W : hi;
 #pragma unroll
       for (int k = 0; k < E; ++k) {
@@ -277,6 +303,7 @@ struct heat_batch {
   long long wait_ns = 5000000000LL;
   int32_t inj_ring_id = -1;  // test hook (heat_batch_inject_stall)
   int graphs = 1;            // capture the run's stream operations and replay them while unchanged
+  int emul_share = -1;       // binary64 tiles of 32 on the integer pipes (-1: the library's choice)
   cudaGraphExec_t graph_exec = nullptr;
   GraphKey graph_key = {};
   int64_t inj_seg = 0, inj_level = 0;
@@ -331,6 +358,17 @@ void arena_free(heat_batch *b, int64_t off, int64_t len) {
 
 int default_T(const heat_batch *b) { return b->dtype == HEAT_F32C ? 32 : 4; }
 
+// Tiles of a unit computed on the integer pipes (binary64, exact reading):
+// every other one unless heat_batch_set_emulation chose a share.
+unsigned batch_emul_mask(const heat_batch *b) {
+  if (b->dtype != HEAT_F64 || b->arith != HEAT_ARITH_EXACT) return 0u;
+  const int share = b->emul_share < 0 ? 16 : b->emul_share;
+  unsigned mask = 0;
+  for (int i = 0; i < 32; ++i)
+    if (((i + 1) * share) / 32 > (i * share) / 32) mask |= 1u << i;
+  return mask;
+}
+
 struct Table {
   std::vector<BRing> rings;
   std::vector<int32_t> ids;  // ring id of each table entry
@@ -368,6 +406,14 @@ Table build_table(const heat_batch *b, int T, int64_t seg_points, F steps_of) {
     d.r = r.r;
     d.rf = r.rf;
     d.parity = r.parity;
+    uint64_t rbits;
+    memcpy(&rbits, &r.r, sizeof(rbits));
+    const int rexp = (int)((rbits >> 52) & 2047);
+    d.mx = heat::emul::prepare_mulx(rbits);
+    if (rexp < 1 || rexp > 2046 || !heat::emul::domain_bounds(rbits, T, d.dom_lo, d.dom_hi)) {
+      d.dom_lo = 1;  // the integer routines take a normal, nonzero r: no integer tiles
+      d.dom_hi = 0;
+    }
     t.rings.push_back(d);
     t.ids.push_back(o.second);
     t.segp.push_back(t.segp.back() + d.nseg);
@@ -436,6 +482,7 @@ int launch_table(heat_batch *b, const Table &t, int T) {
   a.active = (const int32_t *)(b->d_blob + o_act);
   a.L = t.L;
   a.T = T;
+  a.emul_mask = batch_emul_mask(b);
   a.done = b->d_done;
   a.counter = b->d_counter;
   a.st = b->dstat;
@@ -746,6 +793,12 @@ int heat_batch_set_tuning(heat_batch *b, int T, int64_t seg_points) {
   if (T > 0 && 2 * T >= win) return HEAT_EINVAL;
   if (T > 0) b->T = T;
   if (seg_points > 0) b->seg_points = seg_points;
+  return HEAT_OK;
+}
+
+int heat_batch_set_emulation(heat_batch *b, int share) {
+  if (!b || share < -1 || share > 32) return HEAT_EINVAL;
+  b->emul_share = share;
   return HEAT_OK;
 }
 

@@ -21,9 +21,12 @@
 // Binary64, exact reading: a share of the tiles (chosen by a 32-bit mask over
 // tile index mod 32) is computed with the integer-pipe binary64 routines of
 // dp_emul.cuh instead of the FP64 unit; both give the correctly rounded IEEE
-// result, so the bits do not depend on the share.  If any point of an emulated
-// tile leaves the routines' domain, the warp recomputes that tile on the FP64
-// unit from its staged window.
+// result, so the bits do not depend on the share.  Strided layout: if any point
+// of an emulated tile leaves the routines' domain, the warp recomputes that
+// tile on the FP64 unit from its staged window.  Contiguous layout: the tile's
+// values are screened first (zero, or normal within bounds that keep every
+// intermediate of the T steps normal) and advanced in the unpacked form; a
+// tile that fails the screen runs on the FP64 unit.
 //
 // Algorithmic HBM traffic per launch: N points read + N written (16 B per point
 // per T steps in binary64, 8 B in binary32); the halo re-read adds WIN/W.
@@ -53,6 +56,8 @@ struct TBArgs {
   int split;           // other tiles: multiply (and masked final adds) on the integer pipes
   unsigned add_mask;   // registers k whose final add also goes to the integer pipes
   emul::Mul m;         // prepared multiplier r (valid when emul_mask != 0)
+  emul::MulX mx;       // the same for the unpacked form (contiguous layout)
+  int dom_lo, dom_hi;  // unpacked form: input screen for T steps (biased exponents)
 };
 
 template <int MODE>
@@ -209,21 +214,16 @@ __global__ void __launch_bounds__(kWarps * 32) k_tblock_c(TBArgs a) {
     bool dp = true;
     if constexpr (MODE == 0) {
       if ((a.emul_mask >> (unsigned)(tile & 31)) & 1u) {  // this tile on the integer pipes
-        bool bad = false;
-        for (int s = 0; s < a.steps; ++s) P::step_emul(R, a.m, bad);
-        dp = __any_sync(kFull, bad);
-        if (dp) {  // a value left the routines' domain: reload and redo on the FP64 unit
-          if (ws >= 0 && ws + WIN <= N) {
+        bool ok = true;
 #pragma unroll
-            for (int k = 0; k < E; ++k) P::load(R, k, src[base + k]);
-          } else {
-#pragma unroll
-            for (int k = 0; k < E; ++k) {
-              int64_t g = (base + k) % N;
-              if (g < 0) g += N;
-              P::load(R, k, src[g]);
-            }
-          }
+        for (int k = 0; k < E; ++k)
+          ok &= emul::in_domain((uint64_t)__double_as_longlong(P::store(R, k)), a.dom_lo, a.dom_hi);
+        if (__all_sync(kFull, ok)) {  // else the whole tile stays on the FP64 unit
+          if (a.mx.pow2)
+            P::template steps_x<true>(R, a.steps, a.mx);
+          else
+            P::template steps_x<false>(R, a.steps, a.mx);
+          dp = false;
         }
       }
     }
@@ -305,6 +305,9 @@ int launch_tb(heat_ctx *c, const void *src, void *dst, int T, int steps) {
   // the routines take a normal, nonzero multiplier; otherwise every tile uses the FP64 unit
   a.emul_mask = (MODE == 0 && rexp >= 1 && rexp <= 2046) ? tblock_emul_mask(c) : 0u;
   a.m = emul::prepare_mul(rbits);
+  a.mx = emul::prepare_mulx(rbits);
+  // the contiguous layout's unpacked tiles need a nonempty input screen for T steps
+  if (!emul::domain_bounds(rbits, T, a.dom_lo, a.dom_hi) && c->tb_layout == 1) a.emul_mask = 0u;
   a.tile_counter = c->tile_counter;
   // split_level 0: every FP64-unit tile keeps 4 FP64 operations per point;
   // 1: the multiply goes to the integer pipes (3 per point); 1 + j (j = 1..16):
@@ -336,20 +339,21 @@ int launch_tb(heat_ctx *c, const void *src, void *dst, int T, int steps) {
 
 int tblock_window(int dtype) { return dtype == HEAT_F32C ? 32 * TB<2>::E : 32 * TB<0>::E; }
 
-// The automatic integer-pipe share: 3 of every 32 tiles, for binary64 rings
-// under the exact reading in the contiguous layout that give every SM at least
-// 64 of the widest windows (smaller rings finish in a few waves of tiles, where
-// the slower integer tiles would only lengthen the last wave).
+// The automatic integer-pipe share: every other tile (16 of 32), for binary64
+// rings under the exact reading in the contiguous layout that give every SM at
+// least 64 of the widest windows (smaller rings finish in a few waves of tiles,
+// where the slower integer tiles would lengthen the last wave).  Half the tiles
+// on each kind of pipe measured best: the FP64 unit alone and the integer
+// pipes alone advance the ring at about the same rate.
 unsigned tblock_emul_mask(const heat_ctx *c) {
   if (!c->emul_auto) return c->emul_mask;
   if (c->dtype != HEAT_F64 || c->arith != HEAT_ARITH_EXACT || c->tb_layout != 1) return 0u;
   if (c->geo.N < 64LL * c->sms * (32 * 16 - 2 * 8)) return 0u;
-  return (1u << 10) | (1u << 21) | (1u << 31);  // share 3, spread evenly
+  return 0xaaaaaaaau;  // share 16, alternating
 }
 
 // Default depth: binary32 pairs 32 steps per pass; binary64 4, or 8 when part of
-// the tiles run on the integer pipes (their share of the work grows with T,
-// while the FP64 tiles' halo cost grows too; 8 measured best with share 3).
+// the tiles run on the integer pipes (8 measured best with share 16).
 int tblock_default_T(const heat_ctx *c) {
   if (c->dtype == HEAT_F32C) return 32;
   return tblock_emul_mask(c) ? 8 : 4;

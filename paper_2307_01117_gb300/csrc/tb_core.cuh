@@ -197,25 +197,41 @@ struct TBCf64 {
     }
   }
 };
+__device__ __forceinline__ emul::X shfl_x(emul::X v, bool up) {
+  emul::X w;
+  w.m = up ? __shfl_up_sync(kFull, (long long)v.m, 1) : __shfl_down_sync(kFull, (long long)v.m, 1);
+  w.e = up ? __shfl_up_sync(kFull, v.e, 1) : __shfl_down_sync(kFull, v.e, 1);
+  w.pad = 0;
+  return w;
+}
+
 template <int EP>
 struct TBCx<0, EP> : TBCf64<0, EP> {
-  // The step with the integer-pipe binary64 routines (dp_emul.cuh); `bad` is
-  // set when a value leaves their domain and the caller redoes the tile on the
-  // FP64 unit.
-  static __device__ __forceinline__ void step_emul(typename TBCf64<0, EP>::Reg &R, const emul::Mul &m, bool &bad) {
+  // All `steps` steps of a tile on the integer pipes, in the unpacked form of
+  // dp_emul.cuh (the caller has screened the tile's values with in_domain).
+  // The lane's points live in a small local array (w[1..E], halo values in
+  // w[0] and w[E+1]) walked by a loop that is not unrolled, which keeps the
+  // code small enough for the instruction cache beside the FP64-unit tiles.
+  template <bool POW2>
+  static __device__ __forceinline__ void steps_x(typename TBCf64<0, EP>::Reg &R, int steps, const emul::MulX &m) {
     constexpr int E = EP;
-    const double left = __shfl_up_sync(kFull, R.x[E - 1], 1);
-    const double right = __shfl_down_sync(kFull, R.x[0], 1);
-    uint64_t prev = (uint64_t)__double_as_longlong(left);
-    uint64_t cur = (uint64_t)__double_as_longlong(R.x[0]);
+    emul::X w[E + 2];
 #pragma unroll
-    for (int k = 0; k < E; ++k) {
-      const uint64_t nxt = (uint64_t)__double_as_longlong(k + 1 < E ? R.x[k + 1] : right);
-      const uint64_t v = emul::eq2_exact(prev, cur, nxt, m, bad);
-      prev = cur;
-      cur = nxt;
-      R.x[k] = __longlong_as_double((long long)v);
+    for (int k = 0; k < E; ++k) w[k + 1] = emul::unpack((uint64_t)__double_as_longlong(R.x[k]));
+    for (int s = 0; s < steps; ++s) {
+      w[0] = shfl_x(w[E], true);
+      w[E + 1] = shfl_x(w[1], false);
+      emul::X prev = w[0], cur = w[1];
+#pragma unroll 2
+      for (int k = 1; k <= E; ++k) {
+        const emul::X nxt = w[k + 1];
+        w[k] = emul::eq2x<POW2>(prev, cur, nxt, m);
+        prev = cur;
+        cur = nxt;
+      }
     }
+#pragma unroll
+    for (int k = 0; k < E; ++k) R.x[k] = __longlong_as_double((long long)emul::pack(w[k + 1]));
   }
 };
 template <int EP>

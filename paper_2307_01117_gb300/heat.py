@@ -80,6 +80,7 @@ _PROTOS = {
     "heat_batch_set_ctas_per_sm": (_int, [_vp, _int]),
     "heat_batch_set_wait_limit": (_int, [_vp, _i64]),
     "heat_batch_set_graphs": (_int, [_vp, _int]),
+    "heat_batch_set_emulation": (_int, [_vp, _int]),
     "heat_batch_inject_stall": (_int, [_vp, _i32, _i64, _i64]),
     "heat_batch_save": (_int, [_vp]),
     "heat_batch_restore": (_int, [_vp]),
@@ -337,6 +338,10 @@ def heat_batch_set_ctas_per_sm(b: int, ctas: int) -> None:
 
 def heat_batch_set_graphs(b: int, enable: bool) -> None:
     _check(lib().heat_batch_set_graphs(b, int(bool(enable))), "heat_batch_set_graphs")
+
+
+def heat_batch_set_emulation(b: int, share: int) -> None:
+    _check(lib().heat_batch_set_emulation(b, int(share)), "heat_batch_set_emulation")
 
 
 def heat_batch_set_wait_limit(b: int, ns: int) -> None:

@@ -215,3 +215,25 @@ def test_graph_replay_of_a_fixed_batch():
                 assert np.array_equal(bits(H.heat_batch_get(b, rid, nx * np_)), bits(oracle.run(u0, k, nt)))
     finally:
         H.heat_batch_destroy(b)
+
+
+@pytest.mark.parametrize("share", [0, 5, 16, 32])
+def test_integer_pipe_tiles_keep_every_ring_bitwise(share):
+    """Any share of a unit's tiles on the integer pipes gives each ring the
+    oracle's result; power-of-two and general r, zeros and a subnormal ring
+    (which fails the screen and stays on the FP64 unit)."""
+    specs = small_table(30, seed=61 + share, n_hi=60000, nt_hi=60)
+    specs += [(3000, 2, 17, 0.25, np.zeros(6000)),
+              (2048, 1, 9, 0.5, np.full(2048, 5e-310)),
+              (4096, 1, 23, 0.3, workloads.ramp(4096))]
+    b = H.heat_batch_create(sum(nx * np_ + 64 for nx, np_, *_ in specs))
+    try:
+        H.heat_batch_set_emulation(b, share)
+        ids = add_all(b, specs)
+        H.heat_batch_run(b, 0)
+        for rid, (nx, np_, nt, k, u0) in zip(ids, specs):
+            assert np.array_equal(bits(H.heat_batch_get(b, rid, nx * np_)), bits(oracle.run(u0, k, nt))), rid
+        with pytest.raises(H.HeatError):
+            H.heat_batch_set_emulation(b, 33)
+    finally:
+        H.heat_batch_destroy(b)
