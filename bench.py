@@ -162,6 +162,32 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def is_pow2(r: float) -> bool:
+    m, _ = np.frexp(abs(r))
+    return r != 0.0 and m == 0.5
+
+
+ALU_OPS_SRC = ["paper_2307_01117_gb300/csrc/dp_emul.cuh", "paper_2307_01117_gb300/csrc/tb_core.cuh"]
+
+
+def alu_ops(kind: str) -> float | None:
+    """ALU-pipe instructions per point-step of the integer-pipe binary64 routine
+    ("pow2": r = 2^k, "general"), measured with ncu on an all-integer launch and
+    recorded in profiles/alu_ops.json; None if the routine changed since."""
+    p = os.path.join(ROOT, "profiles", "alu_ops.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        rec = json.load(f).get(kind)
+    if not rec:
+        return None
+    h = hashlib.sha256()
+    for s in ALU_OPS_SRC:
+        with open(os.path.join(ROOT, s), "rb") as f:
+            h.update(f.read())
+    return float(rec["alu_inst_per_point_step"]) if rec.get("source_sha256") == h.hexdigest() else None
+
+
 def profile_traffic(kernel: str, workload: str, src_files: list[str]) -> float | None:
     """DRAM bytes per launch from the committed ncu summary (profiles/traffic.json),
     if the kernel's source is unchanged since the counters were taken."""
@@ -321,9 +347,12 @@ class RingRunner:
         # the persistent temporal-blocking form reads and writes the ring once per T-step level)
         passes = {"persist": steps_per_launch, "persist_tb": -(-steps_per_launch // max(1, last["T"]))}.get(form, 1.0)
         alg_bytes = 2.0 * elem * self.n * passes
+        r = self.w["k"] * self.w["dt"] / (self.w["dx"] * self.w["dx"])
         return {"kernel": name, "src": srcs, "launches": launches, "launch_ms": statistics.mean(run_ms) / launches,
                 "point_steps_per_launch": self.n * steps_per_launch, "alg_bytes_per_launch": alg_bytes,
-                "form": form, "T": last["T"], "segments": last["segments"] if form != "plain" else None}
+                "form": form, "T": last["T"], "segments": last["segments"] if form != "plain" else None,
+                "emul_share": self.H.heat_get_emulation(self.h.ctx) if form == "tblock" else 0,
+                "r_pow2": is_pow2(r)}
 
     def config(self):
         w = self.w
@@ -350,6 +379,8 @@ class BatchRunner:
         H.heat_batch_set_stream(self.b, stream)
         self.ids = [H.heat_batch_add(self.b, s.nx, s.np_, s.r, 1.0, 1.0, s.nt, u) for s, u in
                     zip(self.specs, self.inits)]
+        if args.emul >= 0:
+            H.heat_batch_set_emulation(self.b, args.emul)
         if args.T:
             H.heat_batch_set_tuning(self.b, args.T, 0)
             self.tuned = (args.T, 16384)
@@ -394,7 +425,12 @@ class BatchRunner:
                                              "paper_2307_01117_gb300/csrc/tb_core.cuh"],
                 "launches": 1, "launch_ms": statistics.mean(run_ms), "point_steps_per_launch": self.point_steps,
                 "alg_bytes_per_launch": 2.0 * elem * level_points, "form": "batch", "T": T,
-                "segments": self.tuned[1]}
+                "segments": self.tuned[1],
+                # the library's share (16 of 32, 18 for r = 2^k) unless --emul set one
+                "emul_share": (self.args.emul if self.args.emul >= 0 else
+                               (18 if all(is_pow2(s.r) for s in self.specs) else 16))
+                if self.w["dtype"] == "f64" and self.args.arith == "exact" else 0,
+                "r_pow2": all(is_pow2(s.r) for s in self.specs)}
 
     def config(self):
         ns = [s.n for s in self.specs]
@@ -540,6 +576,7 @@ def main() -> int:
     ap.add_argument("--arith", default="exact", choices=["exact", "fma"])
     ap.add_argument("--layout", type=int, default=-1, help="temporal-blocking register layout (0 strided, 1 contiguous)")
     ap.add_argument("--split", type=int, default=0)
+    ap.add_argument("--k", type=float, default=0.0, help="ring workloads: override the diffusivity k (r = k dt/dx^2)")
     ap.add_argument("--emul", type=int, default=-1,
                     help="binary64 tiles of 32 on the integer pipes (-1: the library's choice)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
@@ -551,6 +588,8 @@ def main() -> int:
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     w = dict(WORKLOADS[args.workload])
+    if args.k and w["kind"] in ("ring", "precision"):
+        w["k"] = args.k
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -616,14 +655,32 @@ def main() -> int:
         roofline = {"bound": "alu", "achieved": None, "peak": None, "unit": "G DP-op/s", "frac": None,
                     "note": "mixed binary64 / binary32 requests; the ring and batch lines carry the kernel rooflines"}
     elif w["dtype"] == "f64":
-        ops = DP_OPS[args.arith] * ki["point_steps_per_launch"]
-        dp_peak = 2.0 * sms * pk["sm_max_mhz"] * 1e6 / 1e9
-        achieved = ops / launch_s / 1e9
-        roofline = {"bound": "alu", "achieved": achieved, "peak": dp_peak, "unit": "G DP-op/s",
-                    "frac": achieved / dp_peak,
-                    "peak_src": f"FP64 unit: 2 ops/clk/SM x {sms} SMs x {pk['sm_max_mhz']:.0f} MHz max SM clock "
-                                f"(GB300 nominal 1.25 TFLOP/s FP64)",
-                    "alg_ops_per_launch": ops}
+        # binary64: the FP64 unit's ceiling (2 DP ops/clk/SM) at 4 (exact) or 3 (fused)
+        # DP ops per point-step, plus -- when a share of the tiles runs on the integer
+        # pipes -- the ALU pipes' ceiling (64 lanes/clk/SM) at the integer routine's ALU
+        # instructions per point-step (ncu, profiles/alu_ops.json)
+        clk = pk["sm_max_mhz"] * 1e6
+        f_peak = 2.0 * sms * clk / DP_OPS[args.arith] / 1e9
+        achieved = ki["point_steps_per_launch"] / launch_s / 1e9
+        share = ki.get("emul_share", 0)
+        roofline = {"bound": "alu", "achieved": achieved, "unit": "GLUP/s", "fp64_unit_peak": f_peak,
+                    "emul_share_of_32": share}
+        if share:
+            a_ops = alu_ops("pow2" if ki.get("r_pow2") else "general")
+            i_peak = 64.0 * sms * clk / a_ops / 1e9 if a_ops else None
+            peak = f_peak + i_peak if i_peak else None
+            roofline.update({
+                "peak": peak, "frac": achieved / peak if peak else None, "int_pipes_peak": i_peak,
+                "alu_inst_per_int_point_step": a_ops,
+                "peak_src": f"FP64 unit: 2 DP ops/clk/SM x {sms} SMs x {pk['sm_max_mhz']:.0f} MHz / "
+                            f"{DP_OPS[args.arith]} per point-step, plus ALU pipes: 64 lanes/clk/SM x {sms} SMs x "
+                            f"{pk['sm_max_mhz']:.0f} MHz / {a_ops} ALU instructions per integer point-step "
+                            f"(ncu-measured, profiles/alu_ops.json)"})
+        else:
+            roofline.update({
+                "peak": f_peak, "frac": achieved / f_peak,
+                "peak_src": f"FP64 unit: 2 DP ops/clk/SM x {sms} SMs x {pk['sm_max_mhz']:.0f} MHz max SM clock "
+                            f"/ {DP_OPS[args.arith]} DP ops per point-step (GB300 nominal 1.25 TFLOP/s FP64)"})
     else:
         # binary32 compensated: 13 FP32 operations per point-step (two fused differences
         # and their adds, the sum, the product, TwoSum's six, the correction add)

@@ -170,14 +170,15 @@ HEAT_HD uint64_t eq2_exact(uint64_t ul, uint64_t u, uint64_t ur, const Mul &m, b
 // Unpacked form, for whole temporal-blocking tiles on the integer pipes.
 //
 // A value is held as x = m * 2^e with m a signed (two's complement) 64-bit
-// integer, 2^52 <= |m| <= 2^53, or m = 0 (x = +0) with e very negative.  A
-// tile's values are unpacked once, advanced T steps without packing, and
-// packed once.  The tile's inputs are screened first (in_domain): zero or a
-// normal magnitude within [2^(lo-1023), 2^(hi-1022)), bounds the host derives
-// from T and r so that every intermediate result of the T steps is +0 or a
-// normal, finite binary64 number (no -0: it cannot arise from such inputs).
-// Under that guarantee add/mul/eq2 below are the correctly rounded binary64
-// operations without any range test.
+// integer whose magnitude has its leading 1 at bit 59 (2^59 <= |m| <= 2^60,
+// the 53-bit significand shifted left by 7, low 7 bits zero), or m = 0 (x = +0)
+// with e very negative.  A tile's values are unpacked once, advanced T steps
+// without packing, and packed once.  The tile's inputs are screened first
+// (in_domain): zero or a normal magnitude within [2^(lo-1023), 2^(hi-1022)),
+// bounds the host derives from T and r so that every intermediate result of
+// the T steps is +0 or a normal, finite binary64 number (no -0: it cannot
+// arise from such inputs).  Under that guarantee add/mul/eq2 below are the
+// correctly rounded binary64 operations without any range test.
 struct X {
   int64_t m;
   int32_t e;
@@ -188,18 +189,18 @@ constexpr int32_t kZeroE = -(1 << 24);  // exponent of +0: below every other
 
 HEAT_HD X unpack(uint64_t b) {  // b: +0 or normal
   const int be = (int)(b >> 52) & 2047;
-  const int64_t mag = (int64_t)((b & kFrac) | kImpl);
+  const int64_t mag = (int64_t)(((b & kFrac) | kImpl) << 7);
   X x;
   x.m = be ? ((b >> 63) ? -mag : mag) : 0;
-  x.e = be ? be - 1075 : kZeroE;
+  x.e = be ? be - 1082 : kZeroE;
   x.pad = 0;
   return x;
 }
 
 HEAT_HD uint64_t pack(X x) {
-  const uint64_t mag = (uint64_t)(x.m < 0 ? -x.m : x.m);
-  // biased exponent e + 1075 for |m| in [2^52, 2^53); |m| = 2^53 carries into it
-  const uint64_t v = ((uint64_t)(x.e + 1074) << 52) + mag;
+  const uint64_t mag = (uint64_t)(x.m < 0 ? -x.m : x.m) >> 7;
+  // biased exponent e + 1082 for |m| in [2^59, 2^60); |m| = 2^60 carries into it
+  const uint64_t v = ((uint64_t)(x.e + 1081) << 52) + mag;
   return x.m ? (((uint64_t)x.m & kSign) | v) : 0ull;
 }
 
@@ -209,31 +210,43 @@ HEAT_HD bool in_domain(uint64_t b, int lo, int hi) {
   return b == 0 || (be >= lo && be <= hi);
 }
 
-// x + y, rounded to nearest-even.  The larger-exponent operand is scaled by 2^7
-// (|A| <= 2^60), the other aligned to it by an arithmetic right shift whose lost
-// bits are kept as a sticky 1 in bit 0; the sum (|S| <= 2^61) is shifted left
-// until its leading bit (of |S|, found on the one's complement) sits at bit 61
-// and rounded at bit 9 by floor((S + 255 + bit9) / 2^9), which is round to
-// nearest-even for two's complement values too.  A negative power of two
-// normalises one place high and rounds exactly to |m| = 2^53.
+// Position of the most significant bit that differs from the sign bit (the
+// leading 1 of |v| for v >= 0, of |v| - 1 for v < 0); -1 for v = 0 or -1.
+HEAT_HD int msb_signed(int64_t v) {
+#if defined(__CUDA_ARCH__)
+  unsigned p;
+  asm("bfind.s64 %0, %1;" : "=r"(p) : "l"(v));  // 0xffffffff when v is all sign bits
+  return (int)p;
+#else
+  const uint64_t t = (uint64_t)(v ^ (v >> 63));
+  return t ? 63 - __builtin_clzll(t) : -1;
+#endif
+}
+
+// x + y, rounded to nearest-even.  The smaller-exponent operand is aligned to
+// the other by an arithmetic right shift whose lost bits are kept as a sticky
+// 1 in bit 0 (|A|, |B| <= 2^60, so |S| <= 2^61); the sum is shifted left until
+// its leading bit sits at bit 61 and rounded at bit 9 with
+// floor((S + 255 + bit9) / 2^9) * 2^9, which is round to nearest-even for two's
+// complement values too, then moved to bit 59.  A negative power of two
+// normalises one place high and rounds exactly to |m| = 2^60.
 HEAT_HD X add(X x, X y) {
   const int d = x.e - y.e;
   const bool sw = d < 0;
-  const int64_t mb = sw ? y.m : x.m;
-  const int64_t ms = sw ? x.m : y.m;
+  const int64_t A = sw ? y.m : x.m;
+  const int64_t Bs = sw ? x.m : y.m;
   const int eb = sw ? y.e : x.e;
   int sh = sw ? -d : d;
   sh = sh < 63 ? sh : 63;
-  const int64_t A = (int64_t)((uint64_t)mb << 7);
-  const int64_t Bs = (int64_t)((uint64_t)ms << 7);
   int64_t B = Bs >> sh;
   B |= (int64_t)(((uint64_t)B << sh) != (uint64_t)Bs);  // sticky
   const int64_t S = A + B;
-  const int lz = clz64((uint64_t)(S ^ (S >> 63)));      // 2 .. 64 (64: S = 0)
-  const int64_t Sn = (int64_t)((uint64_t)S << (lz - 2));
+  const int p = msb_signed(S);                           // -1 (S = 0) .. 61
+  const int64_t Sn = (int64_t)((uint64_t)S << (61 - p));
+  const int64_t q = (Sn + 255 + ((Sn >> 9) & 1)) & ~(int64_t)511;
   X r;
-  r.m = (Sn + 255 + ((Sn >> 9) & 1)) >> 9;
-  r.e = S ? eb + 4 - lz : kZeroE;
+  r.m = q >> 2;
+  r.e = p >= 0 ? eb + p - 59 : kZeroE;
   r.pad = 0;
   return r;
 }
@@ -264,19 +277,20 @@ HEAT_HD X scale(X x, const MulX &r) {
   return y;
 }
 
-// r * x, rounded to nearest-even: |m| * 2^10 times r's significand * 2^11 is a
+// r * x, rounded to nearest-even: |m| * 2^3 times r's significand * 2^11 is a
 // 128-bit product in [2^125, 2^127); its high word, normalised to a leading 1 at
-// bit 62 with the remaining bits as a sticky bit, is rounded at bit 10.
+// bit 62 with the remaining bits as a sticky bit, is rounded at bit 10 and
+// moved to bit 59.
 HEAT_HD X mul(X x, const MulX &r) {
   const bool xn = x.m < 0;
-  const uint64_t a = (uint64_t)(xn ? -x.m : x.m) << 10;
+  const uint64_t a = (uint64_t)(xn ? -x.m : x.m) << 3;
   const uint64_t hi = mulhi64(a, r.sig11);
   const uint64_t lo = a * r.sig11;
   const int top = (int)(hi >> 62);  // 1: leading 1 at bit 62; 0: at bit 61 (or x = 0)
   uint64_t s = top ? hi : ((hi << 1) | (lo >> 63));
   const uint64_t rest = top ? lo : (lo << 1);
   s |= (uint64_t)(rest != 0);
-  const uint64_t q = (s + 511 + ((s >> 10) & 1)) >> 10;
+  const uint64_t q = ((s + 511 + ((s >> 10) & 1)) & ~1023ull) >> 3;
   X y;
   y.m = (xn != r.neg) ? -(int64_t)q : (int64_t)q;
   y.e = x.e + r.e + 52 + top;

@@ -364,11 +364,7 @@ int heat_set_emulation(heat_ctx *c, int share) {
   c->emul_auto = share < 0;
   c->emul_share = share;
   if (share < 0) share = 0;
-  // spread `share` set bits evenly over 32 positions
-  unsigned mask = 0;
-  for (int i = 0; i < 32; ++i)
-    if (((i + 1) * share) / 32 > (i * share) / 32) mask |= 1u << i;
-  c->emul_mask = mask;
+  c->emul_mask = heat::emul_share_mask(share);
   return HEAT_OK;
 }
 

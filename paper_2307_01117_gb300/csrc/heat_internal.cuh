@@ -2,6 +2,8 @@
 // translation units of libheat.so.  Not part of the public ABI (include/heat.h).
 #pragma once
 
+#include <string.h>
+
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -114,5 +116,23 @@ constexpr int kSumBlocks = 1024;
 constexpr int kSumThreads = 256;
 
 inline int cuda_status(cudaError_t e) { return e == cudaSuccess ? HEAT_OK : HEAT_ECUDA; }
+
+// `share` set bits spread evenly over tile index mod 32.
+inline unsigned emul_share_mask(int share) {
+  unsigned mask = 0;
+  for (int i = 0; i < 32; ++i)
+    if (((i + 1) * share) / 32 > (i * share) / 32) mask |= 1u << i;
+  return mask;
+}
+
+// The library's share of binary64 tiles on the integer pipes for multiplier r
+// (out of 32): the integer pipes and the FP64 unit each advance the ring at
+// about the same rate, a little faster on the integer side when r = +-2^k (the
+// product then only moves the exponent).
+inline int emul_auto_share(double r) {
+  uint64_t b;
+  memcpy(&b, &r, sizeof(b));
+  return (b & 0x000fffffffffffffull) == 0 ? 18 : 16;
+}
 
 }  // namespace heat

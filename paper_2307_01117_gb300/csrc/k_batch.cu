@@ -58,6 +58,7 @@ struct BRing {
   int parity;         // arena buffer holding the state at the start of the run
   emul::MulX mx;      // r for the integer-pipe tiles (binary64, exact reading)
   int dom_lo, dom_hi; // their input screen for T steps (empty: dom_lo > dom_hi)
+  unsigned emul_mask; // bit (tile mod 32) set: that tile of a unit on the integer pipes
 };
 
 struct BatchArgs {
@@ -69,7 +70,6 @@ struct BatchArgs {
   const int32_t *active;  // rings active at each level (L)
   int L;
   int T;
-  unsigned emul_mask;  // bit (tile mod 32) set: that tile of a unit on the integer pipes
   unsigned *done;
   unsigned long long *counter;
   DevStatus *st;
@@ -197,7 +197,7 @@ __global__ void __launch_bounds__(kBWarps * 32, MODE == 2 ? 3 : 5) k_batch(Batch
       }
       bool dp = true;
       if constexpr (MODE == 0) {
-        if ((a.emul_mask >> (unsigned)(t & 31)) & 1u) {  // this tile on the integer pipes
+        if ((R.emul_mask >> (unsigned)(t & 31)) & 1u) {  // this tile on the integer pipes
           bool ok = true;
 #pragma unroll
           for (int k = 0; k < E; ++k)
@@ -358,15 +358,12 @@ void arena_free(heat_batch *b, int64_t off, int64_t len) {
 
 int default_T(const heat_batch *b) { return b->dtype == HEAT_F32C ? 32 : 4; }
 
-// Tiles of a unit computed on the integer pipes (binary64, exact reading):
-// every other one unless heat_batch_set_emulation chose a share.
-unsigned batch_emul_mask(const heat_batch *b) {
+// Tiles of a ring's units computed on the integer pipes (binary64, exact
+// reading): the library's share for the ring's r unless
+// heat_batch_set_emulation chose one.
+unsigned batch_emul_mask(const heat_batch *b, double r) {
   if (b->dtype != HEAT_F64 || b->arith != HEAT_ARITH_EXACT) return 0u;
-  const int share = b->emul_share < 0 ? 16 : b->emul_share;
-  unsigned mask = 0;
-  for (int i = 0; i < 32; ++i)
-    if (((i + 1) * share) / 32 > (i * share) / 32) mask |= 1u << i;
-  return mask;
+  return heat::emul_share_mask(b->emul_share < 0 ? heat::emul_auto_share(r) : b->emul_share);
 }
 
 struct Table {
@@ -410,6 +407,7 @@ Table build_table(const heat_batch *b, int T, int64_t seg_points, F steps_of) {
     memcpy(&rbits, &r.r, sizeof(rbits));
     const int rexp = (int)((rbits >> 52) & 2047);
     d.mx = heat::emul::prepare_mulx(rbits);
+    d.emul_mask = batch_emul_mask(b, r.r);
     if (rexp < 1 || rexp > 2046 || !heat::emul::domain_bounds(rbits, T, d.dom_lo, d.dom_hi)) {
       d.dom_lo = 1;  // the integer routines take a normal, nonzero r: no integer tiles
       d.dom_hi = 0;
@@ -482,7 +480,6 @@ int launch_table(heat_batch *b, const Table &t, int T) {
   a.active = (const int32_t *)(b->d_blob + o_act);
   a.L = t.L;
   a.T = T;
-  a.emul_mask = batch_emul_mask(b);
   a.done = b->d_done;
   a.counter = b->d_counter;
   a.st = b->dstat;

@@ -339,21 +339,19 @@ int launch_tb(heat_ctx *c, const void *src, void *dst, int T, int steps) {
 
 int tblock_window(int dtype) { return dtype == HEAT_F32C ? 32 * TB<2>::E : 32 * TB<0>::E; }
 
-// The automatic integer-pipe share: every other tile (16 of 32), for binary64
-// rings under the exact reading in the contiguous layout that give every SM at
-// least 64 of the widest windows (smaller rings finish in a few waves of tiles,
-// where the slower integer tiles would lengthen the last wave).  Half the tiles
-// on each kind of pipe measured best: the FP64 unit alone and the integer
-// pipes alone advance the ring at about the same rate.
+// The automatic integer-pipe share (emul_auto_share: 16 or 18 of 32), for
+// binary64 rings under the exact reading in the contiguous layout that give
+// every SM at least 64 of the widest windows (smaller rings finish in a few
+// waves of tiles, where the slower integer tiles would lengthen the last wave).
 unsigned tblock_emul_mask(const heat_ctx *c) {
   if (!c->emul_auto) return c->emul_mask;
   if (c->dtype != HEAT_F64 || c->arith != HEAT_ARITH_EXACT || c->tb_layout != 1) return 0u;
   if (c->geo.N < 64LL * c->sms * (32 * 16 - 2 * 8)) return 0u;
-  return 0xaaaaaaaau;  // share 16, alternating
+  return emul_share_mask(emul_auto_share(c->r));
 }
 
 // Default depth: binary32 pairs 32 steps per pass; binary64 4, or 8 when part of
-// the tiles run on the integer pipes (8 measured best with share 16).
+// the tiles run on the integer pipes (8 measured best with shares 16-18).
 int tblock_default_T(const heat_ctx *c) {
   if (c->dtype == HEAT_F32C) return 32;
   return tblock_emul_mask(c) ? 8 : 4;
