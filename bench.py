@@ -659,15 +659,15 @@ def main() -> int:
         # DP ops per point-step, plus -- when a share of the tiles runs on the integer
         # pipes -- the ALU pipes' ceiling (64 lanes/clk/SM) at the integer routine's ALU
         # instructions per point-step (ncu, profiles/alu_ops.json)
-        clk = pk["sm_max_mhz"] * 1e6
-        f_peak = 2.0 * sms * clk / DP_OPS[args.arith] / 1e9
+        sm_hz = pk["sm_max_mhz"] * 1e6
+        f_peak = 2.0 * sms * sm_hz / DP_OPS[args.arith] / 1e9
         achieved = ki["point_steps_per_launch"] / launch_s / 1e9
         share = ki.get("emul_share", 0)
         roofline = {"bound": "alu", "achieved": achieved, "unit": "GLUP/s", "fp64_unit_peak": f_peak,
                     "emul_share_of_32": share}
         if share:
             a_ops = alu_ops("pow2" if ki.get("r_pow2") else "general")
-            i_peak = 64.0 * sms * clk / a_ops / 1e9 if a_ops else None
+            i_peak = 64.0 * sms * sm_hz / a_ops / 1e9 if a_ops else None
             peak = f_peak + i_peak if i_peak else None
             roofline.update({
                 "peak": peak, "frac": achieved / peak if peak else None, "int_pipes_peak": i_peak,
