@@ -337,7 +337,7 @@ class RingRunner:
         srcs = [f"paper_2307_01117_gb300/csrc/{src}", "paper_2307_01117_gb300/csrc/stencil_ops.cuh"]
         if name in ("k_tblock", "k_cluster", "k_batch"):
             srcs.append("paper_2307_01117_gb300/csrc/tb_core.cuh")
-        if name == "k_tblock":
+        if name in ("k_tblock", "k_batch"):
             srcs.append("paper_2307_01117_gb300/csrc/dp_emul.cuh")
         steps_per_launch = self.nt / launches
         elem = 8.0 if self.w["dtype"] == "f64" else 4.0
@@ -422,7 +422,8 @@ class BatchRunner:
         # every point read and written once per T-step level
         level_points = sum(-(-s.nt // T) * s.n for s in self.specs)
         return {"kernel": "k_batch", "src": ["paper_2307_01117_gb300/csrc/k_batch.cu",
-                                             "paper_2307_01117_gb300/csrc/tb_core.cuh"],
+                                             "paper_2307_01117_gb300/csrc/tb_core.cuh",
+                                             "paper_2307_01117_gb300/csrc/dp_emul.cuh"],
                 "launches": 1, "launch_ms": statistics.mean(run_ms), "point_steps_per_launch": self.point_steps,
                 "alg_bytes_per_launch": 2.0 * elem * level_points, "form": "batch", "T": T,
                 "segments": self.tuned[1],
@@ -535,7 +536,8 @@ class ServeRunner:
         ps = sum(st.gpu_point_steps for st in self.windows)
         per_window = max(1, 2 * ticks // max(1, len(self.windows)))
         return {"kernel": "k_batch", "src": ["paper_2307_01117_gb300/csrc/k_batch.cu",
-                                             "paper_2307_01117_gb300/csrc/tb_core.cuh"],
+                                             "paper_2307_01117_gb300/csrc/tb_core.cuh",
+                                             "paper_2307_01117_gb300/csrc/dp_emul.cuh"],
                 "launches": per_window, "launch_ms": statistics.mean(run_ms) / per_window,
                 "point_steps_per_launch": ps / (2 * ticks), "alg_bytes_per_launch": 0.0, "form": "serve",
                 "T": None, "segments": None}

@@ -167,8 +167,9 @@ int heat_set_segments(heat_ctx *c, int segments);
 /* Binary64 with HEAT_ARITH_EXACT, temporal-blocking form (either layout):
  * compute `share` of every 32 tiles with integer-pipe binary64 arithmetic
  * instead of the FP64 unit (0..32), or -1 (the default) to let the library
- * choose: 16 of 32 with the contiguous layout for rings of at least 64 of the
- * widest windows per SM (with depth 8 unless heat_set_form sets one), else 0.
+ * choose: 18 of 32 for r = +-2^k and 16 otherwise, with the contiguous layout,
+ * for rings of at least 2^19 points (with depth 8 unless heat_set_form sets
+ * one), else 0.
  * GB300's FP64 unit runs at 1/64 of the FP32 rate; the integer pipes are idle
  * during the binary64 update, so splitting the tiles between the two raises
  * throughput.  Both paths give the correctly rounded IEEE result, so the state
