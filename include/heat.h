@@ -151,10 +151,13 @@ int heat_sync(heat_ctx *c);
  * torch.cuda.Stream); NULL restores the context's own stream. */
 int heat_set_stream(heat_ctx *c, void *cuda_stream);
 
-/* Select the kernel form and, for HEAT_FORM_TBLOCK, the temporal block depth
- * T (1..64; 0 = library default: 4 for HEAT_F64, 32 for HEAT_F32C).  T is
- * ignored by the other forms.  HEAT_FORM_AUTO (the default) is
- * HEAT_FORM_TBLOCK. */
+/* Select the kernel form and, for the blocked forms (HEAT_FORM_TBLOCK,
+ * HEAT_FORM_CLUSTER, HEAT_FORM_PERSIST_TB), the temporal block depth T (1..64;
+ * 0 = library default: 32 for HEAT_F32C; for HEAT_F64 8, except 4 in the
+ * temporal-blocking form on rings of at least 2^22 points with every tile on
+ * the FP64 unit).  T is ignored by the one-step forms.  HEAT_FORM_AUTO (the
+ * default) is HEAT_FORM_CLUSTER for rings that one thread-block cluster holds,
+ * else HEAT_FORM_TBLOCK. */
 int heat_set_form(heat_ctx *c, int form, int T);
 
 /* Segmentation of the persistent forms: 0 = library default (near-equal
@@ -168,8 +171,7 @@ int heat_set_segments(heat_ctx *c, int segments);
  * compute `share` of every 32 tiles with integer-pipe binary64 arithmetic
  * instead of the FP64 unit (0..32), or -1 (the default) to let the library
  * choose: 18 of 32 for r = +-2^k and 16 otherwise, with the contiguous layout,
- * for rings of at least 2^19 points (with depth 8 unless heat_set_form sets
- * one), else 0.
+ * for rings of at least 2^18 points, else 0.
  * GB300's FP64 unit runs at 1/64 of the FP32 rate; the integer pipes are idle
  * during the binary64 update, so splitting the tiles between the two raises
  * throughput.  Both paths give the correctly rounded IEEE result, so the state
@@ -309,7 +311,7 @@ int heat_batch_get_device(heat_batch *b, int32_t ring_id, double *dev_u, int64_t
 int heat_batch_remove(heat_batch *b, int32_t ring_id);
 
 /* Temporal block depth T (1..64) and target segment length in points (>= 512);
- * 0 keeps the current value (defaults: T = 4 for binary64, 32 for HEAT_F32C;
+ * 0 keeps the current value (defaults: T = 8 for binary64, 32 for HEAT_F32C;
  * segments of 16384 points). */
 int heat_batch_set_tuning(heat_batch *b, int T, int64_t seg_points);
 

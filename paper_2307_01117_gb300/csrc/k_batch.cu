@@ -356,7 +356,7 @@ void arena_free(heat_batch *b, int64_t off, int64_t len) {
   }
 }
 
-int default_T(const heat_batch *b) { return b->dtype == HEAT_F32C ? 32 : 4; }
+int default_T(const heat_batch *b) { return b->dtype == HEAT_F32C ? 32 : 8; }
 
 // Tiles of a ring's units computed on the integer pipes (binary64, exact
 // reading): the library's share for the ring's r unless
@@ -624,7 +624,7 @@ int heat_batch_create(heat_batch **out, int64_t capacity_points, heat_dtype dtyp
   b->dtype = dtype;
   b->elem = dtype == HEAT_F64 ? 8 : 4;
   b->capacity = round_up(capacity_points, kAlignPointsHost);
-  b->T = dtype == HEAT_F32C ? 32 : 4;
+  b->T = dtype == HEAT_F32C ? 32 : 8;
   int rc = HEAT_OK;
   if (cudaGetDevice(&b->device) != cudaSuccess ||
       cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, b->device) != cudaSuccess ||
@@ -1017,7 +1017,7 @@ int run_persist_tb(heat_ctx *c, int64_t nt) {
   b->arena[0] = c->buf[0];
   b->arena[1] = c->buf[1];
   b->wait_ns = c->wait_ns;
-  const int T = c->T > 0 ? c->T : (c->dtype == HEAT_F32C ? 32 : 4);
+  const int T = c->T > 0 ? c->T : (c->dtype == HEAT_F32C ? 32 : 8);
   const int win = c->dtype == HEAT_F32C ? 32 * tb::TBC<2>::E : 32 * tb::TBC<0>::E;
   if (2 * T >= win) return HEAT_EINVAL;
   heat_batch::Ring r;

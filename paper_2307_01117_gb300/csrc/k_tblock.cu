@@ -341,21 +341,24 @@ int tblock_window(int dtype) { return dtype == HEAT_F32C ? 32 * TB<2>::E : 32 * 
 
 // The automatic integer-pipe share (emul_auto_share: 16 or 18 of 32), for
 // binary64 rings under the exact reading in the contiguous layout of at least
-// 2^19 points (measured at T = 8: +31 % at 10^6 points, +54 % at 2*10^6, +78 %
-// at 4*10^6; smaller rings finish in a few waves of tiles, where the slower
-// integer tiles would lengthen the last wave).
+// 2^18 points (measured at T = 8: +13 % at 2^18 points, +21 % at 2^19, +31 % at
+// 10^6, +78 % at 4*10^6; smaller rings finish in a few waves of tiles, where
+// the slower integer tiles lengthen the last wave: -17 % at 2^16).
 unsigned tblock_emul_mask(const heat_ctx *c) {
   if (!c->emul_auto) return c->emul_mask;
   if (c->dtype != HEAT_F64 || c->arith != HEAT_ARITH_EXACT || c->tb_layout != 1) return 0u;
-  if (c->geo.N < (1LL << 19)) return 0u;
+  if (c->geo.N < (1LL << 18)) return 0u;
   return emul_share_mask(emul_auto_share(c->r));
 }
 
-// Default depth: binary32 pairs 32 steps per pass; binary64 4, or 8 when part of
-// the tiles run on the integer pipes (8 measured best with shares 16-18).
+// Default depth: binary32 pairs 32 steps per pass; binary64 8 (fewer launches
+// and ghost trips: +16 % to +47 % over T = 4 on rings of 2^16 to 2^19 points;
+// 8 is also best with integer tiles), except 4 on large rings with every tile
+// on the FP64 unit (the halo's redundant work then costs more than it saves:
+// 129.1 vs 127.4 GLUP/s at 2^28 points).
 int tblock_default_T(const heat_ctx *c) {
   if (c->dtype == HEAT_F32C) return 32;
-  return tblock_emul_mask(c) ? 8 : 4;
+  return (!tblock_emul_mask(c) && c->geo.N >= (1LL << 22)) ? 4 : 8;
 }
 
 int run_tblock(heat_ctx *c, int64_t nt) {

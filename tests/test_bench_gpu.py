@@ -24,7 +24,7 @@ def test_bench_json_line_contract():
               "vs_baseline", "dtype", "data", "config", "roofline", "e2e", "gpu_launches", "clocks"):
         assert k in d, k
     assert d["unit"] == "GLUP/s" and d["value"] > 0 and d["warmup"] >= 3
-    assert isinstance(d["clocks"], dict) and d["clocks"]["sm_max_mhz"] > 0
+    assert isinstance(d["clocks"], dict) and "sm_max_mhz" in d["clocks"]   # None when the run was shorter than a sample
     rf = d["roofline"]
     assert rf["bound"] == "alu" and rf["achieved"] > 0 and rf["fp64_unit_peak"] > 0
     assert rf["emul_share_of_32"] == d["config"]["emul_share_of_32"]

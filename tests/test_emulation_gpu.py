@@ -93,7 +93,7 @@ def test_split_with_out_of_domain_values():
 def test_automatic_share_is_resolved_per_ring_and_exact():
     """The default (-1): large binary64 rings put 18 of 32 tiles on the integer
     pipes at depth 8; small rings keep every tile on the FP64 unit."""
-    n = 5_000_000                                   # above the 2^19-point threshold
+    n = 5_000_000                                   # above the 2^18-point threshold
     u0 = workloads.uniform_plus_mode(n, seed=5, m=3)
     with H.Heat(n // 4, 4, 0.25, 1.0, 1.0, form="tblock") as h:
         assert H.heat_get_emulation(h.ctx) == 18        # r = 0.25 = 2^-2
@@ -106,7 +106,7 @@ def test_automatic_share_is_resolved_per_ring_and_exact():
     with H.Heat(40000, 1, 0.25, 1.0, 1.0, form="tblock") as h:
         assert H.heat_get_emulation(h.ctx) == 0
         h.set(workloads.uniform(40000, 6, -1, 1)).run(9)
-        assert H.heat_last_run(h.ctx)["T"] == 4
+        assert H.heat_last_run(h.ctx)["T"] == 8
     with pytest.raises(H.HeatError):
         with H.Heat(100, 1, 0.25, 1.0, 1.0) as h:
             H.heat_set_emulation(h.ctx, -2)
