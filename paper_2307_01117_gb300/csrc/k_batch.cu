@@ -125,7 +125,7 @@ __device__ __forceinline__ int64_t floor_index(const int64_t *v, int64_t lo, int
 }
 
 template <int MODE>
-__global__ void __launch_bounds__(kBWarps * 32, MODE == 2 ? 3 : 5) k_batch(BatchArgs a) {  // MODE: 0 exact, 1 fused, 2 binary32
+__global__ void __launch_bounds__(kBWarps * 32, MODE == 2 ? 3 : 6) k_batch(BatchArgs a) {  // MODE: 0 exact, 1 fused, 2 binary32
   using P = tb::TBC<MODE>;  // contiguous per-lane ownership
   using T = typename P::T;
   constexpr int E = P::E;

@@ -182,7 +182,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_tblock(TBArgs a) {
 // Windows are loaded and stored with plain indexed accesses (wrapping around the
 // ring's ends where needed); tiles are claimed from the same launch-wide counter.
 template <int MODE, int EP>
-__global__ void __launch_bounds__(kWarps * 32) k_tblock_c(TBArgs a) {
+__global__ void __launch_bounds__(kWarps * 32, MODE == 2 ? 1 : 8) k_tblock_c(TBArgs a) {
   using P = TBCx<MODE, EP>;
   using T = typename P::T;
   constexpr int E = P::E;
