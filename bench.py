@@ -23,7 +23,10 @@ value = ring point-steps / second (GLUP/s, the paper's "cells processed per
 second", Section 6), timed with CUDA events on the work's stream, 3+ warm-ups,
 inputs larger than L2.  `e2e` is the same metric through the C ABI with host
 buffers: the initial state is copied in from pinned host memory and the final
-state read back inside the timed region.
+state read back inside the timed region.  `cpu_baseline` is the CPU oracle,
+single-threaded, on a bounded sample; `cpu_threaded` is the paper's parallel
+algorithm (one host thread per segment, SPSC ghost queues) on every host core,
+on the same sample.
 
 Under torchrun (N > 1) every rank runs its own independent replica on its own
 GPU (replicas only: the ring is not sharded across GPUs): weak scaling, no
@@ -264,6 +267,31 @@ def cpu_baseline(w: dict, seconds: float = 12.0) -> dict:
     return {"value": n * steps / total / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"first {n} points of the initial state as a ring of their own x {steps} steps "
                       f"({'binary32 compensated' if w['dtype'] == 'f32c' else 'binary64'}), {total:.1f} s on 1 host core"}
+
+
+def cpu_threaded(w: dict, seconds: float = 8.0) -> dict | None:
+    """The paper's parallel algorithm on every host core (oracle/heat_threaded.c:
+    one thread per segment, mutex/condition-variable SPSC ghost queues, Section 2)
+    on the same bounded sample as cpu_baseline; binary64 ring workloads only."""
+    if w["kind"] not in ("ring",) or w["dtype"] != "f64":
+        return None
+    import oracle
+    cores = os.cpu_count() or 1
+    n = min(w["nx"] * w["np"], 1 << 22) // cores * cores
+    w2 = dict(w)
+    w2["nx"], w2["np"] = n, 1
+    u = initial_state(w2)
+    r = oracle.coef(w["k"], w["dt"], w["dx"])
+    steps, total, chunk = 0, 0.0, 16
+    while total < seconds:
+        t0 = time.perf_counter()
+        u = oracle.run_threaded(u, cores, r, chunk)
+        total += time.perf_counter() - t0
+        steps += chunk
+    return {"value": n * steps / total / 1e9, "unit": UNIT, "cores": cores,
+            "kind": "threaded SPSC-queue stepper (Section 2): one thread per segment",
+            "sample": f"first {n} points of the initial state as a ring of their own, {cores} segments x "
+                      f"{steps} steps (binary64), {total:.1f} s on {cores} host cores"}
 
 
 def run_reference(args, w: dict, rank: int) -> None:
@@ -713,9 +741,10 @@ def main() -> int:
         e2e = {"value": world * runner.point_steps * k_e2e / dt_e2e / 1e9, "unit": UNIT, "h2d_bytes_per_step": bi,
                "d2h_bytes_per_step": bo, "steps": k_e2e}
 
-    cb = None
+    cb = ct = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and w["kind"] != "serve":
         cb = cpu_baseline(w)
+        ct = cpu_threaded(w)
 
     launches = args.steps * (ki["launches"] + (2 if w["kind"] in ("ring", "precision") else 0))
     if rank == 0:
@@ -726,7 +755,8 @@ def main() -> int:
             "metric": METRIC[w["dtype"]], "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64" if w["dtype"] == "f64" else "f32", "data": "synthetic",
-            "config": cfg, "roofline": roofline, "roofline_hbm": roof_hbm, "cpu_baseline": cb, "e2e": e2e,
+            "config": cfg, "roofline": roofline, "roofline_hbm": roof_hbm, "cpu_baseline": cb, "cpu_threaded": ct,
+            "e2e": e2e,
             "gpu_launches": launches, "clocks": clk,
         }
         if w["kind"] == "precision":

@@ -11,7 +11,9 @@ on first use and exposes numpy-level wrappers:
 * ``coef(k, dt, dx)``        -- r = k*dt/dx^2 (Eq. 2, h^2 reading of the denominator)
 * ``run(u0, r, nt, fma)``    -- nt steps of Eq. 2 on the periodic ring (unsegmented)
 * ``run_segmented(u0, np_, r, nt)`` -- the segmented algorithm with SPSC ghost queues
-  (Section 2, parallel algorithm)
+  (Section 2, parallel algorithm), single-threaded
+* ``run_threaded(u0, np_, r, nt)`` -- the same with one host thread per segment
+  (``heat_threaded.c``; the threaded CPU baseline)
 * ``cone(u0, r, nt, idx, fma)`` -- u^nt at selected points from their light cone
 * ``run_f32c(u0, rf, nt, T)`` -- FP32 storage with the compensated update
 * ``total(u)``               -- left-to-right FP64 sum (conservation diagnostic)
@@ -27,20 +29,22 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "heat_oracle.c")
+_SRC_THREADED = os.path.join(_HERE, "heat_threaded.c")
 _BUILD = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_BUILD, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-CFLAGS = ["-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", "-std=c99"]
+CFLAGS = ["-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", "-std=gnu99", "-pthread"]
 
 
 def build(force: bool = False) -> str:
     """Compile heat_oracle.c into oracle/_build/liboracle.so (idempotent)."""
     os.makedirs(_BUILD, exist_ok=True)
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+    srcs = [_SRC, _SRC_THREADED]
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < max(os.path.getmtime(p) for p in srcs):
         tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", *CFLAGS, "-o", tmp, _SRC, "-lm"])
+        subprocess.check_call(["gcc", *CFLAGS, "-o", tmp, *srcs, "-lm"])
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -59,6 +63,8 @@ def _load():
         lib.heat_oracle_run.argtypes = [vp, vp, i64, d, i64, ip]
         lib.heat_oracle_run_segmented.restype = ip
         lib.heat_oracle_run_segmented.argtypes = [vp, i64, i32, d, i64]
+        lib.heat_threaded_run.restype = ip
+        lib.heat_threaded_run.argtypes = [vp, i64, i32, d, i64]
         lib.heat_oracle_cone.restype = ip
         lib.heat_oracle_cone.argtypes = [vp, i64, d, i64, vp, i64, vp, ip]
         lib.heat_oracle_run_f32c.restype = ip
@@ -96,6 +102,18 @@ def run_segmented(u0, np_: int, r: float, nt: int) -> np.ndarray:
     rc = _load().heat_oracle_run_segmented(u.ctypes.data, u.size // np_, int(np_), float(r), int(nt))
     if rc != 0:
         raise ValueError(f"heat_oracle_run_segmented failed ({rc})")
+    return u
+
+
+def run_threaded(u0, np_: int, r: float, nt: int) -> np.ndarray:
+    """The segmented algorithm with one host thread per segment and mutex/condition-
+    variable SPSC ghost queues (heat_threaded.c: the threaded CPU baseline)."""
+    u = _f64(u0)
+    if u.size % np_ != 0:
+        raise ValueError("ring length must be np_ * nx")
+    rc = _load().heat_threaded_run(u.ctypes.data, u.size // np_, int(np_), float(r), int(nt))
+    if rc != 0:
+        raise ValueError(f"heat_threaded_run failed ({rc})")
     return u
 
 

@@ -279,6 +279,16 @@ def test_segmented_equals_unsegmented(np_, nx):
         assert np.array_equal(a, b)
 
 
+@pytest.mark.parametrize("np_,nx", [(1, 1), (1, 9), (2, 1), (3, 5), (4, 1000), (7, 3), (16, 4), (32, 257)])
+def test_threaded_baseline_equals_unsegmented(np_, nx):
+    """The threaded CPU baseline (one host thread per segment, mutex/condition-
+    variable queues) computes the oracle's result bitwise, whatever the
+    thread interleaving."""
+    u0 = workloads.uniform(np_ * nx, 23, -1, 1)
+    for nt in (0, 1, 40):
+        assert np.array_equal(oracle.run_threaded(u0, np_, 0.27, nt), oracle.run(u0, 0.27, nt))
+
+
 @pytest.mark.parametrize("n,nt", [(1, 3), (5, 4), (64, 10), (300, 40)])
 @pytest.mark.parametrize("fma", [False, True])
 def test_cone_equals_full_run(n, nt, fma):
