@@ -380,7 +380,11 @@ class RingRunner:
                 "point_steps_per_launch": self.n * steps_per_launch, "alg_bytes_per_launch": alg_bytes,
                 "form": form, "T": last["T"], "segments": last["segments"] if form != "plain" else None,
                 "emul_share": self.H.heat_get_emulation(self.h.ctx) if form == "tblock" else 0,
-                "r_pow2": is_pow2(r)}
+                "r_pow2": is_pow2(r),
+                # FP64-unit operations per point-step: for r = 2^k the contiguous temporal-blocking
+                # tiles multiply by moving the exponent on the integer pipes
+                "dp_ops": 3 if (form == "tblock" and self.args.layout != 0 and self.args.arith == "exact"
+                                and is_pow2(r)) else DP_OPS[self.args.arith]}
 
     def config(self):
         w = self.w
@@ -455,9 +459,9 @@ class BatchRunner:
                 "launches": 1, "launch_ms": statistics.mean(run_ms), "point_steps_per_launch": self.point_steps,
                 "alg_bytes_per_launch": 2.0 * elem * level_points, "form": "batch", "T": T,
                 "segments": self.tuned[1],
-                # the library's share (16 of 32, 18 for r = 2^k) unless --emul set one
+                # the library's share (16 of 32) unless --emul set one
                 "emul_share": (self.args.emul if self.args.emul >= 0 else
-                               (18 if all(is_pow2(s.r) for s in self.specs) else 16))
+                               16)
                 if self.w["dtype"] == "f64" and self.args.arith == "exact" else 0,
                 "r_pow2": all(is_pow2(s.r) for s in self.specs)}
 
@@ -690,11 +694,12 @@ def main() -> int:
         # pipes -- the ALU pipes' ceiling (64 lanes/clk/SM) at the integer routine's ALU
         # instructions per point-step (ncu, profiles/alu_ops.json)
         sm_hz = pk["sm_max_mhz"] * 1e6
-        f_peak = 2.0 * sms * sm_hz / DP_OPS[args.arith] / 1e9
+        dp_ops = ki.get("dp_ops", DP_OPS[args.arith])
+        f_peak = 2.0 * sms * sm_hz / dp_ops / 1e9
         achieved = ki["point_steps_per_launch"] / launch_s / 1e9
         share = ki.get("emul_share", 0)
         roofline = {"bound": "alu", "achieved": achieved, "unit": "GLUP/s", "fp64_unit_peak": f_peak,
-                    "emul_share_of_32": share}
+                    "fp64_ops_per_point_step": dp_ops, "emul_share_of_32": share}
         if share:
             a_ops = alu_ops("pow2" if ki.get("r_pow2") else "general")
             i_peak = 64.0 * sms * sm_hz / a_ops / 1e9 if a_ops else None
@@ -703,14 +708,14 @@ def main() -> int:
                 "peak": peak, "frac": achieved / peak if peak else None, "int_pipes_peak": i_peak,
                 "alu_inst_per_int_point_step": a_ops,
                 "peak_src": f"FP64 unit: 2 DP ops/clk/SM x {sms} SMs x {pk['sm_max_mhz']:.0f} MHz / "
-                            f"{DP_OPS[args.arith]} per point-step, plus ALU pipes: 64 lanes/clk/SM x {sms} SMs x "
+                            f"{dp_ops} per point-step, plus ALU pipes: 64 lanes/clk/SM x {sms} SMs x "
                             f"{pk['sm_max_mhz']:.0f} MHz / {a_ops} ALU instructions per integer point-step "
                             f"(ncu-measured, profiles/alu_ops.json)"})
         else:
             roofline.update({
                 "peak": f_peak, "frac": achieved / f_peak,
                 "peak_src": f"FP64 unit: 2 DP ops/clk/SM x {sms} SMs x {pk['sm_max_mhz']:.0f} MHz max SM clock "
-                            f"/ {DP_OPS[args.arith]} DP ops per point-step (GB300 nominal 1.25 TFLOP/s FP64)"})
+                            f"/ {dp_ops} DP ops per point-step (GB300 nominal 1.25 TFLOP/s FP64)"})
     else:
         # binary32 compensated: 13 FP32 operations per point-step (two fused differences
         # and their adds, the sum, the product, TwoSum's six, the correction add)

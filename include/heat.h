@@ -170,7 +170,7 @@ int heat_set_segments(heat_ctx *c, int segments);
 /* Binary64 with HEAT_ARITH_EXACT, temporal-blocking form (either layout):
  * compute `share` of every 32 tiles with integer-pipe binary64 arithmetic
  * instead of the FP64 unit (0..32), or -1 (the default) to let the library
- * choose: 18 of 32 for r = +-2^k and 16 otherwise, with the contiguous layout,
+ * choose: 16 of 32 with the contiguous layout,
  * for rings of at least 2^18 points, else 0.
  * GB300's FP64 unit runs at 1/64 of the FP32 rate; the integer pipes are idle
  * during the binary64 update, so splitting the tiles between the two raises
@@ -180,8 +180,10 @@ int heat_set_segments(heat_ctx *c, int segments);
  * results, signed zeros) is recomputed on the FP64 unit.  Contiguous layout: a
  * tile runs on the integer pipes only if its values pass a screen (+0, or
  * normal magnitudes within bounds derived from T and r that keep every
- * intermediate result normal), else on the FP64 unit.  HEAT_EINVAL outside
- * -1..32. */
+ * intermediate result normal), else on the FP64 unit.  For r = +-2^k the
+ * contiguous layout's FP64-unit tiles that pass the same screen multiply by
+ * moving the exponent with an integer add (three FP64-unit operations per
+ * point instead of four; the same bits).  HEAT_EINVAL outside -1..32. */
 int heat_set_emulation(heat_ctx *c, int share);
 
 /* The share of 32 tiles the temporal-blocking form computes on the integer

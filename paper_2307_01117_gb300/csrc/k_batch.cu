@@ -59,6 +59,7 @@ struct BRing {
   emul::MulX mx;      // r for the integer-pipe tiles (binary64, exact reading)
   int dom_lo, dom_hi; // their input screen for T steps (empty: dom_lo > dom_hi)
   unsigned emul_mask; // bit (tile mod 32) set: that tile of a unit on the integer pipes
+  int p2_hi_add, p2_hi_xor;  // r = +-2^k: screened FP64-unit tiles move the product's exponent
 };
 
 struct BatchArgs {
@@ -197,13 +198,16 @@ __global__ void __launch_bounds__(kBWarps * 32, MODE == 2 ? 3 : 6) k_batch(Batch
       }
       bool dp = true;
       if constexpr (MODE == 0) {
-        if ((R.emul_mask >> (unsigned)(t & 31)) & 1u) {  // this tile on the integer pipes
+        const bool int_tile = (R.emul_mask >> (unsigned)(t & 31)) & 1u;
+        if (int_tile || R.mx.pow2) {
           bool ok = true;
 #pragma unroll
           for (int k = 0; k < E; ++k)
             ok &= emul::in_domain((uint64_t)__double_as_longlong(P::store(reg, k)), R.dom_lo, R.dom_hi);
           if (__all_sync(0xffffffffu, ok)) {
-            if (R.mx.pow2)
+            if (!int_tile)  // r = +-2^k on the FP64 unit: the product moves the exponent
+              for (int s = 0; s < steps; ++s) P::step_p2(reg, R.p2_hi_add, R.p2_hi_xor);
+            else if (R.mx.pow2)
               P::template steps_x<true>(reg, steps, R.mx);
             else
               P::template steps_x<false>(reg, steps, R.mx);
@@ -408,6 +412,8 @@ Table build_table(const heat_batch *b, int T, int64_t seg_points, F steps_of) {
     const int rexp = (int)((rbits >> 52) & 2047);
     d.mx = heat::emul::prepare_mulx(rbits);
     d.emul_mask = batch_emul_mask(b, r.r);
+    d.p2_hi_add = (rexp - 1023) * (1 << 20);
+    d.p2_hi_xor = (rbits >> 63) ? (int)0x80000000u : 0;
     if (rexp < 1 || rexp > 2046 || !heat::emul::domain_bounds(rbits, T, d.dom_lo, d.dom_hi)) {
       d.dom_lo = 1;  // the integer routines take a normal, nonzero r: no integer tiles
       d.dom_hi = 0;

@@ -14,6 +14,7 @@
 // writes that reuse its buffer.  The ring is periodic within the cluster: the
 // neighbours of CTA 0 are CTAs C-1 and 1.
 #include <cooperative_groups.h>
+#include <string.h>
 
 #include "tb_core.cuh"
 
@@ -33,6 +34,9 @@ struct ClusterArgs {
   int64_t nt;
   double r;
   float rf;
+  int p2;                  // binary64, r = +-2^k: screened windows multiply on the integer pipes
+  int dom_lo, dom_hi;      // the screen for T steps (biased exponents)
+  int p2_hi_add, p2_hi_xor;
 };
 
 template <int MODE, int EP>
@@ -88,7 +92,20 @@ __global__ void __launch_bounds__(kCWarps * 32) k_cluster(ClusterArgs a) {
         }
         P::load(R, k, v);
       }
-      for (int s = 0; s < steps; ++s) P::step(R, lane, a.r, a.rf);
+      bool p2 = false;
+      if constexpr (MODE == 0) {
+        if (a.p2) {
+          bool ok = true;
+#pragma unroll
+          for (int k = 0; k < E; ++k)
+            ok &= emul::in_domain((uint64_t)__double_as_longlong(P::store(R, k)), a.dom_lo, a.dom_hi);
+          p2 = __all_sync(0xffffffffu, ok);
+        }
+        if (p2)
+          for (int s = 0; s < steps; ++s) P::step_p2(R, a.p2_hi_add, a.p2_hi_xor);
+      }
+      if (!p2)
+        for (int s = 0; s < steps; ++s) P::step(R, lane, a.r, a.rf);
 #pragma unroll
       for (int k = 0; k < E; ++k) {
         const int i = E * lane + k;
@@ -125,6 +142,15 @@ int launch_cluster(heat_ctx *c, int C, int T, int64_t nt) {
   a.nt = nt;
   a.r = c->r;
   a.rf = c->rf;
+  uint64_t rbits;
+  memcpy(&rbits, &c->r, sizeof(rbits));
+  const int rexp = (int)((rbits >> 52) & 2047);
+  // r = +-2^k, exact reading: windows whose values pass the integer tiles'
+  // screen move the product's exponent with an integer add (eq2_exact_pow2)
+  a.p2 = MODE == 0 && rexp >= 1 && rexp <= 2046 && (rbits & 0x000fffffffffffffull) == 0 &&
+         emul::domain_bounds(rbits, T, a.dom_lo, a.dom_hi);
+  a.p2_hi_add = (rexp - 1023) * (1 << 20);
+  a.p2_hi_xor = (rbits >> 63) ? (int)0x80000000u : 0;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(C);
   cfg.blockDim = dim3(kCWarps * 32);

@@ -58,6 +58,8 @@ struct TBArgs {
   emul::Mul m;         // prepared multiplier r (valid when emul_mask != 0)
   emul::MulX mx;       // the same for the unpacked form (contiguous layout)
   int dom_lo, dom_hi;  // unpacked form: input screen for T steps (biased exponents)
+  int p2_fp64;         // r = +-2^k: screened FP64-unit tiles multiply on the integer pipes
+  int p2_hi_add, p2_hi_xor;
 };
 
 template <int MODE>
@@ -213,13 +215,16 @@ __global__ void __launch_bounds__(kWarps * 32, MODE == 2 ? 1 : 8) k_tblock_c(TBA
     }
     bool dp = true;
     if constexpr (MODE == 0) {
-      if ((a.emul_mask >> (unsigned)(tile & 31)) & 1u) {  // this tile on the integer pipes
+      const bool int_tile = (a.emul_mask >> (unsigned)(tile & 31)) & 1u;
+      if (int_tile || a.p2_fp64) {
         bool ok = true;
 #pragma unroll
         for (int k = 0; k < E; ++k)
           ok &= emul::in_domain((uint64_t)__double_as_longlong(P::store(R, k)), a.dom_lo, a.dom_hi);
-        if (__all_sync(kFull, ok)) {  // else the whole tile stays on the FP64 unit
-          if (a.mx.pow2)
+        if (__all_sync(kFull, ok)) {  // else the whole tile takes the plain FP64-unit steps
+          if (!int_tile)
+            for (int s = 0; s < a.steps; ++s) P::step_p2(R, a.p2_hi_add, a.p2_hi_xor);
+          else if (a.mx.pow2)
             P::template steps_x<true>(R, a.steps, a.mx);
           else
             P::template steps_x<false>(R, a.steps, a.mx);
@@ -307,7 +312,13 @@ int launch_tb(heat_ctx *c, const void *src, void *dst, int T, int steps) {
   a.m = emul::prepare_mul(rbits);
   a.mx = emul::prepare_mulx(rbits);
   // the contiguous layout's unpacked tiles need a nonempty input screen for T steps
-  if (!emul::domain_bounds(rbits, T, a.dom_lo, a.dom_hi) && c->tb_layout == 1) a.emul_mask = 0u;
+  const bool dom = emul::domain_bounds(rbits, T, a.dom_lo, a.dom_hi);
+  if (!dom && c->tb_layout == 1) a.emul_mask = 0u;
+  // r = +-2^k, exact reading: the FP64-unit tiles that pass the same screen move
+  // the product's exponent with an integer add (3 FP64-unit operations per point)
+  a.p2_fp64 = MODE == 0 && dom && a.mx.pow2 && c->tb_layout == 1;
+  a.p2_hi_add = (int)(((int64_t)rexp - 1023) * (1 << 20));
+  a.p2_hi_xor = (rbits >> 63) ? (int)0x80000000u : 0;
   a.tile_counter = c->tile_counter;
   // split_level 0: every FP64-unit tile keeps 4 FP64 operations per point;
   // 1: the multiply goes to the integer pipes (3 per point); 1 + j (j = 1..16):
@@ -339,7 +350,7 @@ int launch_tb(heat_ctx *c, const void *src, void *dst, int T, int steps) {
 
 int tblock_window(int dtype) { return dtype == HEAT_F32C ? 32 * TB<2>::E : 32 * TB<0>::E; }
 
-// The automatic integer-pipe share (emul_auto_share: 16 or 18 of 32), for
+// The automatic integer-pipe share (emul_auto_share: 16 of 32), for
 // binary64 rings under the exact reading in the contiguous layout of at least
 // 2^18 points (measured at T = 8: +13 % at 2^18 points, +21 % at 2^19, +31 % at
 // 10^6, +78 % at 4*10^6; smaller rings finish in a few waves of tiles, where

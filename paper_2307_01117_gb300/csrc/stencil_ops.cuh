@@ -24,6 +24,19 @@ __device__ __forceinline__ double eq2_fma(double ul, double u, double ur, double
   return __fma_rn(r, t2, u);
 }
 
+// Eq. 2, exact reading, for r = +-2^k on operands screened so that every
+// intermediate value is +0 or normal with room below (the integer-pipe tiles'
+// screen): r * t2 is then exact and only moves t2's exponent, so it is done on
+// the high word with an integer add (hi_add = k << 20) and a sign flip
+// (hi_xor), +0 staying +0.  Three FP64-unit operations per point instead of
+// four; the same bits as eq2_exact.
+__device__ __forceinline__ double eq2_exact_pow2(double ul, double u, double ur, int hi_add, int hi_xor) {
+  const double t2 = __dadd_rn(__fma_rn(-2.0, u, ul), ur);
+  const int hi = __double2hiint(t2);
+  const double t3 = __hiloint2double(hi == 0 ? 0 : ((hi + hi_add) ^ hi_xor), __double2loint(t2));
+  return __dadd_rn(u, t3);
+}
+
 template <bool FMA>
 __device__ __forceinline__ double eq2(double ul, double u, double ur, double r) {
   return FMA ? eq2_fma(ul, u, ur, r) : eq2_exact(ul, u, ur, r);

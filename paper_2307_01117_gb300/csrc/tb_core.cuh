@@ -207,6 +207,22 @@ __device__ __forceinline__ emul::X shfl_x(emul::X v, bool up) {
 
 template <int EP>
 struct TBCx<0, EP> : TBCf64<0, EP> {
+  // One step on the FP64 unit for r = +-2^k and a screened tile (the multiply
+  // moves the exponent on the integer pipes: eq2_exact_pow2).
+  static __device__ __forceinline__ void step_p2(typename TBCf64<0, EP>::Reg &R, int hi_add, int hi_xor) {
+    constexpr int E = EP;
+    const double left = __shfl_up_sync(kFull, R.x[E - 1], 1);
+    const double right = __shfl_down_sync(kFull, R.x[0], 1);
+    double prev = left;
+#pragma unroll
+    for (int k = 0; k < E; ++k) {
+      const double nxt = k + 1 < E ? R.x[k + 1] : right;
+      const double v = eq2_exact_pow2(prev, R.x[k], nxt, hi_add, hi_xor);
+      prev = R.x[k];
+      R.x[k] = v;
+    }
+  }
+
   // All `steps` steps of a tile on the integer pipes, in the unpacked form of
   // dp_emul.cuh (the caller has screened the tile's values with in_domain).
   // The lane's points live in a small local array (w[1..E], halo values in

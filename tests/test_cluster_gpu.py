@@ -45,6 +45,22 @@ def test_paper_small_ring_in_one_launch():
     assert np.array_equal(got.view(np.uint64), oracle.run(u0, 0.5, 100).view(np.uint64))
 
 
+@pytest.mark.parametrize("r", [0.5, 0.25, -0.125])
+def test_cluster_power_of_two_r_with_out_of_domain_windows(r):
+    """r = +-2^k: windows whose values pass the screen multiply by moving the
+    exponent; windows with zeros, -0 or subnormals take the plain FP64 steps.
+    Both give the oracle's bits."""
+    n = 20000
+    u0 = workloads.uniform(n, 77, -1, 1)
+    u0[100:180] = 0.0
+    u0[3000] = -0.0
+    u0[9000:9010] = 3e-310
+    u0[15000:15020] = 1e-200
+    for T in (0, 8):
+        got, _ = run(u0, 4, r, 37, T)
+        assert np.array_equal(got.view(np.uint64), oracle.run(u0, r, 37).view(np.uint64)), T
+
+
 @pytest.mark.parametrize("n", [1, 5, 1000, 10000, 60000])
 def test_cluster_f32c_bitwise(n):
     u0 = workloads.uniform(n, 11 + n, -1, 1)

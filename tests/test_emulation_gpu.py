@@ -91,12 +91,12 @@ def test_split_with_out_of_domain_values():
 
 
 def test_automatic_share_is_resolved_per_ring_and_exact():
-    """The default (-1): large binary64 rings put 18 of 32 tiles on the integer
+    """The default (-1): large binary64 rings put 16 of 32 tiles on the integer
     pipes at depth 8; small rings keep every tile on the FP64 unit."""
     n = 5_000_000                                   # above the 2^18-point threshold
     u0 = workloads.uniform_plus_mode(n, seed=5, m=3)
     with H.Heat(n // 4, 4, 0.25, 1.0, 1.0, form="tblock") as h:
-        assert H.heat_get_emulation(h.ctx) == 18        # r = 0.25 = 2^-2
+        assert H.heat_get_emulation(h.ctx) == 16
         h.set(u0).run(20)
         assert H.heat_last_run(h.ctx)["T"] == 8
         got = h.get()
@@ -110,3 +110,18 @@ def test_automatic_share_is_resolved_per_ring_and_exact():
     with pytest.raises(H.HeatError):
         with H.Heat(100, 1, 0.25, 1.0, 1.0) as h:
             H.heat_set_emulation(h.ctx, -2)
+
+
+@pytest.mark.parametrize("r", [0.5, 0.25, 0.125, -0.25])
+@pytest.mark.parametrize("share", [0, 16])
+def test_power_of_two_r_fp64_tiles(r, share):
+    """r = +-2^k: screened FP64-unit tiles move the product's exponent on the
+    integer pipes; tiles with zeros, -0, subnormals or tiny values take the
+    plain FP64 steps.  Bitwise the oracle either way."""
+    n = 3 * 4096 + 101
+    u0 = workloads.uniform(n, 5, -1, 1)
+    u0[10:50] = 0.0
+    u0[2000] = -0.0
+    u0[5000:5004] = 2e-310
+    u0[7000:7010] = 1e-250
+    assert np.array_equal(bits(run(u0, r, 29, 8, share)), bits(oracle.run(u0, r, 29)))
