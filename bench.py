@@ -381,9 +381,9 @@ class RingRunner:
                 "form": form, "T": last["T"], "segments": last["segments"] if form != "plain" else None,
                 "emul_share": self.H.heat_get_emulation(self.h.ctx) if form == "tblock" else 0,
                 "r_pow2": is_pow2(r),
-                # FP64-unit operations per point-step: for r = 2^k the contiguous temporal-blocking
-                # tiles multiply by moving the exponent on the integer pipes
-                "dp_ops": 3 if (form == "tblock" and self.args.layout != 0 and self.args.arith == "exact"
+                # FP64-unit operations per point-step: for r = 2^k every form but the strided
+                # temporal-blocking layout multiplies by moving the exponent on the integer pipes
+                "dp_ops": 3 if (not (form == "tblock" and self.args.layout == 0) and self.args.arith == "exact"
                                 and is_pow2(r)) else DP_OPS[self.args.arith]}
 
     def config(self):

@@ -8,6 +8,9 @@
 // (wrapping at 0 and N-1).  The fewer than 64 trailing points are done by
 // scalar threads.  Algorithmic traffic: 8 bytes read + 8 bytes written per
 // point-step for binary64, 4 + 4 for binary32.
+#include <string.h>
+
+#include "dp_emul.cuh"
 #include "heat_internal.cuh"
 #include "stencil_ops.cuh"
 
@@ -22,9 +25,22 @@ constexpr int kPlainThreads = 256;
 // while the FP64 unit drains.
 constexpr int kU64 = 4;
 
-template <bool FMA>
+// For r = +-2^k under the exact reading (P2): a group whose values, edge
+// neighbours included, pass the integer-pipe screen for one step takes the
+// multiply as an exponent add on the integer pipes (eq2_exact_pow2: 3 FP64-unit
+// operations per point); other groups, leftover tiles and the tail the plain
+// exact update.
+struct P2Args {
+  int dom_lo, dom_hi, hi_add, hi_xor;
+};
+
+__device__ __forceinline__ bool p2_ok(double x, const P2Args &p) {
+  return emul::in_domain((uint64_t)__double_as_longlong(x), p.dom_lo, p.dom_hi);
+}
+
+template <bool FMA, bool P2>
 __global__ void __launch_bounds__(kPlainThreads) k_plain_f64(const double *__restrict__ u, double *__restrict__ v,
-                                                             int64_t N, double r) {
+                                                             int64_t N, double r, P2Args p2a) {
   const int lane = threadIdx.x & 31;
   const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t warp = gtid >> 5;
@@ -39,6 +55,13 @@ __global__ void __launch_bounds__(kPlainThreads) k_plain_f64(const double *__res
     double eleft = 0.0, eright = 0.0;
     if (lane == 0) eleft = u[b0 == 0 ? N - 1 : b0 - 1];
     if (lane == 31) eright = u[b0 + 64 * kU64 == N ? 0 : b0 + 64 * kU64];
+    bool p2 = false;
+    if constexpr (P2) {
+      bool ok = p2_ok(eleft, p2a) && p2_ok(eright, p2a);
+#pragma unroll
+      for (int j = 0; j < kU64; ++j) ok = ok && p2_ok(x[j].x, p2a) && p2_ok(x[j].y, p2a);
+      p2 = __all_sync(kFull, ok);
+    }
 #pragma unroll
     for (int j = 0; j < kU64; ++j) {
       double left = __shfl_up_sync(kFull, x[j].y, 1);
@@ -48,8 +71,13 @@ __global__ void __launch_bounds__(kPlainThreads) k_plain_f64(const double *__res
       if (lane == 0) left = j > 0 ? prev_y : eleft;
       if (lane == 31) right = j + 1 < kU64 ? next_x : eright;
       double2 y;
-      y.x = eq2<FMA>(left, x[j].x, x[j].y, r);
-      y.y = eq2<FMA>(x[j].x, x[j].y, right, r);
+      if (P2 && p2) {
+        y.x = eq2_exact_pow2(left, x[j].x, x[j].y, p2a.hi_add, p2a.hi_xor);
+        y.y = eq2_exact_pow2(x[j].x, x[j].y, right, p2a.hi_add, p2a.hi_xor);
+      } else {
+        y.x = eq2<FMA>(left, x[j].x, x[j].y, r);
+        y.y = eq2<FMA>(x[j].x, x[j].y, right, r);
+      }
       __stcs(reinterpret_cast<double2 *>(v + b0 + 64 * j) + lane, y);
     }
   }
@@ -165,10 +193,21 @@ int run_plain(heat_ctx *c, int64_t nt) {
     void *dst = c->buf[c->cur ^ 1];
     if (c->dtype == HEAT_F64) {
       const int grid = plain_grid(c, (N >> 6) / kU64 > 0 ? (N >> 6) / kU64 : 1);
+      uint64_t rbits;
+      memcpy(&rbits, &c->r, sizeof(rbits));
+      const int rexp = (int)((rbits >> 52) & 2047);
+      P2Args p2a = {1, 0, (rexp - 1023) * (1 << 20), (rbits >> 63) ? (int)0x80000000u : 0};
+      const bool p2 = c->arith == HEAT_ARITH_EXACT && rexp >= 1 && rexp <= 2046 &&
+                      (rbits & 0x000fffffffffffffull) == 0 && emul::domain_bounds(rbits, 1, p2a.dom_lo, p2a.dom_hi);
       if (c->arith == HEAT_ARITH_FMA)
-        k_plain_f64<true><<<grid, kPlainThreads, 0, c->stream>>>((const double *)src, (double *)dst, N, c->r);
+        k_plain_f64<true, false><<<grid, kPlainThreads, 0, c->stream>>>((const double *)src, (double *)dst, N, c->r,
+                                                                       p2a);
+      else if (p2)
+        k_plain_f64<false, true><<<grid, kPlainThreads, 0, c->stream>>>((const double *)src, (double *)dst, N, c->r,
+                                                                       p2a);
       else
-        k_plain_f64<false><<<grid, kPlainThreads, 0, c->stream>>>((const double *)src, (double *)dst, N, c->r);
+        k_plain_f64<false, false><<<grid, kPlainThreads, 0, c->stream>>>((const double *)src, (double *)dst, N, c->r,
+                                                                        p2a);
     } else {
       const int grid = plain_grid(c, (N >> 7) / kU > 0 ? (N >> 7) / kU : 1);
       k_plain_f32c<<<grid, kPlainThreads, 0, c->stream>>>((const float *)src, (float *)dst, N, c->rf);

@@ -61,6 +61,24 @@ def test_f64_exact_bitwise(form, T, n, np_):
         assert same_bits(got, ref), (n, np_, nt, r, int(np.sum(got != ref)))
 
 
+@pytest.mark.parametrize("form,T", FORMS_F64 + [("cluster", 0), ("tblock", 0)])
+@pytest.mark.parametrize("r", [0.5, 0.25, -0.25])
+def test_f64_power_of_two_r_with_out_of_domain_values(form, T, r):
+    """r = +-2^k: tiles, groups or windows whose values pass the integer-pipe
+    screen move the product's exponent on the integer pipes; the ones holding
+    +0 next to -0, subnormals or tiny values take the plain FP64 update."""
+    n = 4 * 4096 + 64                     # within the cluster form's limit
+    u0 = workloads.uniform(n, 4242, -1, 1)
+    u0[64:200] = 0.0
+    u0[1000] = -0.0
+    u0[5000:5008] = 4e-310
+    u0[9000:9050] = 1e-290
+    u0[12000:12003] = 1e300
+    for nt in (1, 19):
+        ref = oracle.run(u0, r, nt)
+        assert same_bits(run_gpu(u0, 4, r, nt, form, T), ref), (form, T, nt)
+
+
 @pytest.mark.parametrize("form,T", FORMS_F64)
 def test_paper_config_small_ring(form, T):
     """np=4 x nx=1000, nt=100, k=0.5, dt=dx=1, u[g]=g (Section 2's initial condition)."""
