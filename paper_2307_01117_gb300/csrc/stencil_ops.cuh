@@ -67,6 +67,69 @@ __device__ __forceinline__ void eq2_f32c(float hl, float h, float hr, float ll, 
   l_out = __fadd_rn(l, e);
 }
 
+// The same step on two points at once: each 64-bit operand holds two binary32
+// values, and every operation but the product is the paired IEEE binary32
+// operation with round-to-nearest (add/sub/fma .rn.f32x2), so each half is
+// bitwise the scalar eq2_f32c.  The product rf*d is two scalar multiplies: a
+// paired multiply feeding the paired add that follows was measured to round
+// differently in some cases (as if the two had been fused), which the scalar
+// form does not.  Paired instructions halve the issue slots the compensated
+// update needs.
+__device__ __forceinline__ unsigned long long f2_add(unsigned long long a, unsigned long long b) {
+  unsigned long long d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ unsigned long long f2_sub(unsigned long long a, unsigned long long b) {
+  unsigned long long d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ unsigned long long f2_mul(unsigned long long a, unsigned long long b) {
+  unsigned long long d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ unsigned long long f2_fma(unsigned long long a, unsigned long long b,
+                                                     unsigned long long c) {
+  unsigned long long d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ unsigned long long f2_pack(float lo, float hi) {
+  unsigned long long d;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(d) : "f"(lo), "f"(hi));
+  return d;
+}
+__device__ __forceinline__ float f2_lo(unsigned long long v) {
+  float a, b;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+  return a;
+}
+__device__ __forceinline__ float f2_hi(unsigned long long v) {
+  float a, b;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+  return b;
+}
+
+__device__ __forceinline__ void eq2_f32c_x2(unsigned long long hl, unsigned long long h, unsigned long long hr,
+                                            unsigned long long ll, unsigned long long l, unsigned long long lr,
+                                            float rf, unsigned long long &h_out, unsigned long long &l_out) {
+  // (-2, -2) built by a move, so that it is a register operand: an integer
+  // literal in a paired floating-point instruction would not mean two -2.0f
+  const unsigned long long m2 = f2_pack(-2.0f, -2.0f);
+  const unsigned long long dh = f2_add(f2_fma(m2, h, hl), hr);
+  const unsigned long long dl = f2_add(f2_fma(m2, l, ll), lr);
+  const unsigned long long d = f2_add(dh, dl);
+  const unsigned long long inc = f2_pack(__fmul_rn(rf, f2_lo(d)), __fmul_rn(rf, f2_hi(d)));
+  // TwoSum(h, inc)
+  const unsigned long long s = f2_add(h, inc);
+  const unsigned long long bb = f2_sub(s, h);
+  const unsigned long long e = f2_add(f2_sub(h, f2_sub(s, bb)), f2_sub(inc, bb));
+  h_out = s;
+  l_out = f2_add(l, e);
+}
+
 // End of a temporal block: the stored binary32 value RN(h + l).
 __device__ __forceinline__ float f32c_store(float h, float l) { return __fadd_rn(h, l); }
 

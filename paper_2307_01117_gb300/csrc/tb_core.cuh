@@ -258,29 +258,41 @@ template <int EP>
 struct TBCx<2, EP> {
   using T = float;
   static constexpr int E = EP;
+  static constexpr int H = EP / 2;
+  // Pair j holds the lane's points j and j + H (low and high half), so the
+  // left and right neighbours of pair j are pairs j - 1 and j + 1: the whole
+  // step runs on paired binary32 instructions (eq2_f32c_x2); only the two
+  // pairs at the ends are assembled from single values each step.
   struct Reg {
-    float h[E];
-    float l[E];
+    unsigned long long h[H];
+    unsigned long long l[H];
   };
   static __device__ __forceinline__ void load(Reg &R, int k, float v) {
-    R.h[k] = v;
-    R.l[k] = 0.0f;
+    const int j = k < H ? k : k - H;
+    R.h[j] = k < H ? f2_pack(v, f2_hi(R.h[j])) : f2_pack(f2_lo(R.h[j]), v);
+    R.l[j] = 0ull;
   }
-  static __device__ __forceinline__ float store(const Reg &R, int k) { return f32c_store(R.h[k], R.l[k]); }
+  static __device__ __forceinline__ float store(const Reg &R, int k) {
+    const int j = k < H ? k : k - H;
+    return k < H ? f32c_store(f2_lo(R.h[j]), f2_lo(R.l[j])) : f32c_store(f2_hi(R.h[j]), f2_hi(R.l[j]));
+  }
   static __device__ __forceinline__ void step(Reg &R, int, double, float rf) {
-    const float lh = __shfl_up_sync(kFull, R.h[E - 1], 1), ll = __shfl_up_sync(kFull, R.l[E - 1], 1);
-    const float rh = __shfl_down_sync(kFull, R.h[0], 1), rl = __shfl_down_sync(kFull, R.l[0], 1);
-    float ph = lh, pl = ll;
+    // point -1 (lane - 1's point E - 1) and point E (lane + 1's point 0)
+    const float ph = __shfl_up_sync(kFull, f2_hi(R.h[H - 1]), 1), pl = __shfl_up_sync(kFull, f2_hi(R.l[H - 1]), 1);
+    const float nh = __shfl_down_sync(kFull, f2_lo(R.h[0]), 1), nl = __shfl_down_sync(kFull, f2_lo(R.l[0]), 1);
+    // neighbours of the end pairs: (point -1, point H - 1) and (point H, point E)
+    unsigned long long prev_h = f2_pack(ph, f2_lo(R.h[H - 1])), prev_l = f2_pack(pl, f2_lo(R.l[H - 1]));
+    const unsigned long long last_h = f2_pack(f2_hi(R.h[0]), nh), last_l = f2_pack(f2_hi(R.l[0]), nl);
 #pragma unroll
-    for (int k = 0; k < E; ++k) {
-      const float nh = k + 1 < E ? R.h[k + 1] : rh;
-      const float nl = k + 1 < E ? R.l[k + 1] : rl;
-      float hn, ln;
-      eq2_f32c(ph, R.h[k], nh, pl, R.l[k], nl, rf, hn, ln);
-      ph = R.h[k];
-      pl = R.l[k];
-      R.h[k] = hn;
-      R.l[k] = ln;
+    for (int j = 0; j < H; ++j) {
+      const unsigned long long nxt_h = j + 1 < H ? R.h[j + 1] : last_h;
+      const unsigned long long nxt_l = j + 1 < H ? R.l[j + 1] : last_l;
+      unsigned long long hn, ln;
+      eq2_f32c_x2(prev_h, R.h[j], nxt_h, prev_l, R.l[j], nxt_l, rf, hn, ln);
+      prev_h = R.h[j];
+      prev_l = R.l[j];
+      R.h[j] = hn;
+      R.l[j] = ln;
     }
   }
 };
