@@ -459,9 +459,8 @@ class BatchRunner:
                 "launches": 1, "launch_ms": statistics.mean(run_ms), "point_steps_per_launch": self.point_steps,
                 "alg_bytes_per_launch": 2.0 * elem * level_points, "form": "batch", "T": T,
                 "segments": self.tuned[1],
-                # the library's share (16 of 32) unless --emul set one
-                "emul_share": (self.args.emul if self.args.emul >= 0 else
-                               16)
+                # the library's adaptive split (-1) unless --emul set a share
+                "emul_share": (self.args.emul if self.args.emul >= 0 else -1)
                 if self.w["dtype"] == "f64" and self.args.arith == "exact" else 0,
                 "r_pow2": all(is_pow2(s.r) for s in self.specs)}
 

@@ -170,8 +170,10 @@ int heat_set_segments(heat_ctx *c, int segments);
 /* Binary64 with HEAT_ARITH_EXACT, temporal-blocking form (either layout):
  * compute `share` of every 32 tiles with integer-pipe binary64 arithmetic
  * instead of the FP64 unit (0..32), or -1 (the default) to let the library
- * choose: 16 of 32 with the contiguous layout,
- * for rings of at least 2^18 points, else 0.
+ * choose: with the contiguous layout, for rings of at least 2^18 points, half
+ * of the warps take tiles for the integer pipes from the end of the ring while
+ * the other half take tiles for the FP64 unit from the start, so the split
+ * follows the two engines' speeds; else every tile on the FP64 unit.
  * GB300's FP64 unit runs at 1/64 of the FP32 rate; the integer pipes are idle
  * during the binary64 update, so splitting the tiles between the two raises
  * throughput.  Both paths give the correctly rounded IEEE result, so the state
@@ -187,8 +189,8 @@ int heat_set_segments(heat_ctx *c, int segments);
 int heat_set_emulation(heat_ctx *c, int share);
 
 /* The share of 32 tiles the temporal-blocking form computes on the integer
- * pipes for this ring as configured now (the automatic choice resolved), into
- * *share.  HEAT_EINVAL for null arguments. */
+ * pipes for this ring as configured now, into *share: 0..32, or -1 when the
+ * library's adaptive split applies.  HEAT_EINVAL for null arguments. */
 int heat_get_emulation(const heat_ctx *c, int *share);
 
 /* Binary64 with HEAT_ARITH_EXACT, temporal-blocking form with the strided
@@ -334,9 +336,12 @@ int heat_batch_set_graphs(heat_batch *b, int enable);
 
 /* Binary64 batches (exact reading): `share` of every 32 tiles of each work unit
  * computed on the integer pipes instead of the FP64 unit (0..32), or -1 (the
- * default) for the library's choice, 16.  A tile runs there only if its values
- * pass the screen described at heat_set_emulation; the state is bitwise the
- * same for every share.  HEAT_EINVAL outside -1..32. */
+ * default) for the library's choice: within each unit, half of the warps take
+ * tiles for the integer pipes from the end and the others tiles for the FP64
+ * unit from the start, so the split follows the two engines' speeds.  A tile
+ * runs on the integer pipes only if its values pass the screen described at
+ * heat_set_emulation; the state is bitwise the same for every share.
+ * HEAT_EINVAL outside -1..32. */
 int heat_batch_set_emulation(heat_batch *b, int share);
 
 /* Upper bound, in nanoseconds, on a unit's wait for its neighbours' previous

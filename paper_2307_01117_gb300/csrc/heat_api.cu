@@ -370,7 +370,9 @@ int heat_set_emulation(heat_ctx *c, int share) {
 
 int heat_get_emulation(const heat_ctx *c, int *share) {
   if (!c || !share) return HEAT_EINVAL;
-  *share = __builtin_popcount(heat::tblock_emul_mask(c));
+  const unsigned mask = heat::tblock_emul_mask(c);
+  // the library's choice is adaptive (two-ended tile claiming): reported as -1
+  *share = c->emul_auto && mask ? -1 : __builtin_popcount(mask);
   return HEAT_OK;
 }
 

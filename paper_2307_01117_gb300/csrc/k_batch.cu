@@ -71,6 +71,7 @@ struct BatchArgs {
   const int32_t *active;  // rings active at each level (L)
   int L;
   int T;
+  int dual;  // binary64 under the library's share: two-ended tile claiming within units
   unsigned *done;
   unsigned long long *counter;
   DevStatus *st;
@@ -133,7 +134,7 @@ __global__ void __launch_bounds__(kBWarps * 32, MODE == 2 ? 3 : 6) k_batch(Batch
   constexpr int WIN = 32 * E;
   __shared__ long long s_ring, s_level, s_lo, s_hi, s_steps, s_seg;
   __shared__ int s_stop;
-  __shared__ int s_tile;  // the unit's tiles are claimed by the CTA's warps in order
+  __shared__ unsigned long long s_tile;  // the unit's tiles are claimed by the CTA's warps (see below)
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
   const int64_t total = a.levp[a.L];
@@ -179,11 +180,28 @@ __global__ void __launch_bounds__(kBWarps * 32, MODE == 2 ? 3 : 6) k_batch(Batch
     const int64_t lo = s_lo, hi = s_hi, n = R.n;
     const int steps = (int)s_steps;
     const int64_t ntile = (hi - lo + W - 1) / W;
+    // Binary64 rings under the library's share: two-ended claiming within the
+    // unit (integer-pipe warps from the end, FP64-unit warps from the start,
+    // one 64-bit shared counter), so the split follows the engines' speeds.
+    // Otherwise tiles in order, R.emul_mask choosing their engine.
+    const bool dual = MODE == 0 && a.dual && R.emul_mask != 0u;
+    const bool int_warp = dual && (((blockIdx.x ^ wib) & 1) != 0);
     for (;;) {
-      int tc = 0;
-      if (lane == 0) tc = atomicAdd(&s_tile, 1);
-      const int64_t t = __shfl_sync(0xffffffffu, tc, 0);
-      if (t >= ntile) break;
+      unsigned long long tc = 0;
+      if (lane == 0) tc = atomicAdd(&s_tile, int_warp ? (1ull << 32) : 1ull);
+      tc = __shfl_sync(0xffffffffu, tc, 0);
+      int64_t t;
+      bool int_tile;
+      if (dual) {
+        const int64_t f = (int64_t)(tc & 0xffffffffull), b = (int64_t)(tc >> 32);
+        if (f + b >= ntile) break;
+        t = int_warp ? ntile - 1 - b : f;
+        int_tile = int_warp;
+      } else {
+        t = (int64_t)tc;
+        if (t >= ntile) break;
+        int_tile = MODE == 0 && ((R.emul_mask >> (unsigned)(t & 31)) & 1u);
+      }
       const int64_t ws = lo + t * W - a.T;
       typename P::Reg reg;
       const bool inside = ws >= 0 && ws + WIN <= n;
@@ -198,7 +216,6 @@ __global__ void __launch_bounds__(kBWarps * 32, MODE == 2 ? 3 : 6) k_batch(Batch
       }
       bool dp = true;
       if constexpr (MODE == 0) {
-        const bool int_tile = (R.emul_mask >> (unsigned)(t & 31)) & 1u;
         if (int_tile || R.mx.pow2) {
           bool ok = true;
 #pragma unroll
@@ -486,6 +503,7 @@ int launch_table(heat_batch *b, const Table &t, int T) {
   a.active = (const int32_t *)(b->d_blob + o_act);
   a.L = t.L;
   a.T = T;
+  a.dual = b->emul_share < 0;
   a.done = b->d_done;
   a.counter = b->d_counter;
   a.st = b->dstat;

@@ -59,6 +59,7 @@ struct TBArgs {
   emul::MulX mx;       // the same for the unpacked form (contiguous layout)
   int dom_lo, dom_hi;  // unpacked form: input screen for T steps (biased exponents)
   int p2_fp64;         // r = +-2^k: screened FP64-unit tiles multiply on the integer pipes
+  int dual;            // two-ended claiming instead of emul_mask (see k_tblock_c)
   int p2_hi_add, p2_hi_xor;
 };
 
@@ -194,11 +195,29 @@ __global__ void __launch_bounds__(kWarps * 32, MODE == 2 ? 1 : 8) k_tblock_c(TBA
   T *dst = (T *)a.dst;
   const int64_t N = a.N;
   const int W = WIN - 2 * a.T;
+  // Two-ended claiming (binary64, a.dual): integer-pipe warps take tiles from
+  // the end of the range and FP64-unit warps from the start, through one 64-bit
+  // counter (low half: tiles taken from the start, high half: from the end), so
+  // the split between the engines follows their speeds and both finish
+  // together.  Warp kinds alternate with CTA and warp index, which puts both
+  // kinds on every SM sub-partition.
+  const bool int_warp = MODE == 0 && a.dual && (((blockIdx.x ^ (threadIdx.x >> 5)) & 1) != 0);
   for (;;) {
     unsigned long long t = 0;
-    if (lane == 0) t = atomicAdd(a.tile_counter, 1ull);
-    const int64_t tile = (int64_t)__shfl_sync(kFull, t, 0);
-    if (tile >= a.ntiles) break;
+    if (lane == 0) t = atomicAdd(a.tile_counter, int_warp ? (1ull << 32) : 1ull);
+    t = __shfl_sync(kFull, t, 0);
+    int64_t tile;
+    bool int_tile;
+    if (MODE == 0 && a.dual) {
+      const int64_t f = (int64_t)(t & 0xffffffffull), b = (int64_t)(t >> 32);
+      if (f + b >= a.ntiles) break;
+      tile = int_warp ? a.ntiles - 1 - b : f;
+      int_tile = int_warp;
+    } else {
+      tile = (int64_t)t;
+      if (tile >= a.ntiles) break;
+      int_tile = MODE == 0 && ((a.emul_mask >> (unsigned)(tile & 31)) & 1u);
+    }
     const int64_t ws = tile * (int64_t)W - a.T;
     const int64_t base = ws + (int64_t)E * lane;
     typename P::Reg R;
@@ -215,7 +234,6 @@ __global__ void __launch_bounds__(kWarps * 32, MODE == 2 ? 1 : 8) k_tblock_c(TBA
     }
     bool dp = true;
     if constexpr (MODE == 0) {
-      const bool int_tile = (a.emul_mask >> (unsigned)(tile & 31)) & 1u;
       if (int_tile || a.p2_fp64) {
         bool ok = true;
 #pragma unroll
@@ -317,6 +335,8 @@ int launch_tb(heat_ctx *c, const void *src, void *dst, int T, int steps) {
   // r = +-2^k, exact reading: the FP64-unit tiles that pass the same screen move
   // the product's exponent with an integer add (3 FP64-unit operations per point)
   a.p2_fp64 = MODE == 0 && dom && a.mx.pow2 && c->tb_layout == 1;
+  // the library's choice of share: adaptive, by claiming from both ends
+  a.dual = MODE == 0 && c->emul_auto && a.emul_mask != 0u && c->tb_layout == 1;
   a.p2_hi_add = (int)(((int64_t)rexp - 1023) * (1 << 20));
   a.p2_hi_xor = (rbits >> 63) ? (int)0x80000000u : 0;
   a.tile_counter = c->tile_counter;

@@ -91,12 +91,13 @@ def test_split_with_out_of_domain_values():
 
 
 def test_automatic_share_is_resolved_per_ring_and_exact():
-    """The default (-1): large binary64 rings put 16 of 32 tiles on the integer
-    pipes at depth 8; small rings keep every tile on the FP64 unit."""
+    """The default (-1): large binary64 rings split their tiles adaptively
+    between the integer pipes and the FP64 unit at depth 8; small rings keep
+    every tile on the FP64 unit."""
     n = 5_000_000                                   # above the 2^18-point threshold
     u0 = workloads.uniform_plus_mode(n, seed=5, m=3)
     with H.Heat(n // 4, 4, 0.25, 1.0, 1.0, form="tblock") as h:
-        assert H.heat_get_emulation(h.ctx) == 16
+        assert H.heat_get_emulation(h.ctx) == -1        # adaptive: tiles claimed from both ends
         h.set(u0).run(20)
         assert H.heat_last_run(h.ctx)["T"] == 8
         got = h.get()
