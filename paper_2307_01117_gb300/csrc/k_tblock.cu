@@ -383,13 +383,15 @@ unsigned tblock_emul_mask(const heat_ctx *c) {
 }
 
 // Default depth: binary32 pairs 32 steps per pass; binary64 8 (fewer launches
-// and ghost trips: +16 % to +47 % over T = 4 on rings of 2^16 to 2^19 points;
-// 8 is also best with integer tiles), except 4 on large rings with every tile
-// on the FP64 unit (the halo's redundant work then costs more than it saves:
-// 129.1 vs 127.4 GLUP/s at 2^28 points).
+// and ghost trips: +16 % to +47 % over T = 4 on rings of 2^16 to 2^19 points),
+// 12 on rings of at least 2^22 points with integer tiles (the integer tiles
+// unpack and pack once per pass: +1.3 % over 8 at 2^28 points), and 4 on such
+// rings with every tile on the FP64 unit (the halo's redundant work then costs
+// more than it saves: 129.1 vs 127.4 GLUP/s at 2^28 points).
 int tblock_default_T(const heat_ctx *c) {
   if (c->dtype == HEAT_F32C) return 32;
-  return (!tblock_emul_mask(c) && c->geo.N >= (1LL << 22)) ? 4 : 8;
+  if (c->geo.N < (1LL << 22)) return 8;
+  return tblock_emul_mask(c) ? 12 : 4;
 }
 
 int run_tblock(heat_ctx *c, int64_t nt) {

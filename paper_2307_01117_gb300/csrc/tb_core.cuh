@@ -238,7 +238,7 @@ struct TBCx<0, EP> : TBCf64<0, EP> {
       w[0] = shfl_x(w[E], true);
       w[E + 1] = shfl_x(w[1], false);
       emul::X prev = w[0], cur = w[1];
-#pragma unroll 2
+#pragma unroll 4
       for (int k = 1; k <= E; ++k) {
         const emul::X nxt = w[k + 1];
         w[k] = emul::eq2x<POW2>(prev, cur, nxt, m);

@@ -99,7 +99,7 @@ def test_automatic_share_is_resolved_per_ring_and_exact():
     with H.Heat(n // 4, 4, 0.25, 1.0, 1.0, form="tblock") as h:
         assert H.heat_get_emulation(h.ctx) == -1        # adaptive: tiles claimed from both ends
         h.set(u0).run(20)
-        assert H.heat_last_run(h.ctx)["T"] == 8
+        assert H.heat_last_run(h.ctx)["T"] == 12          # at least 2^22 points
         got = h.get()
         H.heat_set_emulation(h.ctx, 0)
         assert H.heat_get_emulation(h.ctx) == 0
