@@ -231,6 +231,23 @@ def replica_throughput(point_steps_per_step: float, steps: int, ms_max: float, w
 # ---------------------------------------------------------------------------------------------
 # CPU oracle baseline
 
+def host_cpu() -> str:
+    """The host CPU's model (from /proc/cpuinfo where it is there) and core count."""
+    seen = {}
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if ":" in line:
+                    key, val = (x.strip() for x in line.split(":", 1))
+                    seen.setdefault(key.lower(), val)
+    except OSError:
+        pass
+    import platform
+    model = seen.get("model name") or " ".join(
+        f"{k} {seen[k]}" for k in ("cpu implementer", "cpu part") if k in seen)
+    return f"{model or platform.processor() or platform.machine()} ({platform.machine()}), {os.cpu_count()} cores"
+
+
 def cpu_baseline(w: dict, seconds: float = 12.0) -> dict:
     """The CPU oracle, as it stands, single-threaded on a bounded sample of the
     workload, stepped until about `seconds` have passed."""
@@ -248,7 +265,7 @@ def cpu_baseline(w: dict, seconds: float = 12.0) -> dict:
             total += time.perf_counter() - t0
             done_pts += spec.n * spec.nt
             rings += 1
-        return {"value": done_pts / total / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+        return {"value": done_pts / total / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle", "host": host_cpu(),
                 "sample": f"the first {rings} rings of the table, all their steps, {total:.1f} s on 1 host core"}
     n = min(w["nx"] * w["np"], 1 << 22)
     w2 = dict(w)
@@ -264,7 +281,7 @@ def cpu_baseline(w: dict, seconds: float = 12.0) -> dict:
             u = oracle.run(u, r, chunk)
         total += time.perf_counter() - t0
         steps += chunk
-    return {"value": n * steps / total / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+    return {"value": n * steps / total / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle", "host": host_cpu(),
             "sample": f"first {n} points of the initial state as a ring of their own x {steps} steps "
                       f"({'binary32 compensated' if w['dtype'] == 'f32c' else 'binary64'}), {total:.1f} s on 1 host core"}
 
@@ -288,7 +305,7 @@ def cpu_threaded(w: dict, seconds: float = 8.0) -> dict | None:
         u = oracle.run_threaded(u, cores, r, chunk)
         total += time.perf_counter() - t0
         steps += chunk
-    return {"value": n * steps / total / 1e9, "unit": UNIT, "cores": cores,
+    return {"value": n * steps / total / 1e9, "unit": UNIT, "cores": cores, "host": host_cpu(),
             "kind": "threaded SPSC-queue stepper (Section 2): one thread per segment",
             "sample": f"first {n} points of the initial state as a ring of their own, {cores} segments x "
                       f"{steps} steps (binary64), {total:.1f} s on {cores} host cores"}
