@@ -370,11 +370,13 @@ int launch_tb(heat_ctx *c, const void *src, void *dst, int T, int steps) {
 
 int tblock_window(int dtype) { return dtype == HEAT_F32C ? 32 * TB<2>::E : 32 * TB<0>::E; }
 
-// The automatic integer-pipe share (emul_auto_share: 16 of 32), for
-// binary64 rings under the exact reading in the contiguous layout of at least
-// 2^18 points (measured at T = 8: +13 % at 2^18 points, +21 % at 2^19, +31 % at
-// 10^6, +78 % at 4*10^6; smaller rings finish in a few waves of tiles, where
-// the slower integer tiles lengthen the last wave: -17 % at 2^16).
+// Integer tiles under the library's choice: for binary64 rings under the
+// exact reading in the contiguous layout of at least 2^18 points; a nonzero
+// mask here switches the launch to the adaptive two-ended split (a.dual), the
+// mask's own share (emul_auto_share) only standing for "on".  Measured with
+// the split against every tile on the FP64 unit at T = 8: +14 % at 2^18
+// points, +83 % at 10^6; smaller rings finish in a few waves of tiles, where
+// the slower integer tiles lengthen the last one (-28 % at 2^16).
 unsigned tblock_emul_mask(const heat_ctx *c) {
   if (!c->emul_auto) return c->emul_mask;
   if (c->dtype != HEAT_F64 || c->arith != HEAT_ARITH_EXACT || c->tb_layout != 1) return 0u;
