@@ -40,6 +40,7 @@ void free_ctx(heat_ctx *c) {
   if (c->seg_start) cudaFree(c->seg_start);
   if (c->partials) cudaFree(c->partials);
   if (c->hsum) cudaFreeHost(c->hsum);
+  if (c->xstage) cudaFree(c->xstage);
   if (c->tile_counter) cudaFree(c->tile_counter);
   if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
   heat::free_persist_tb(c);
@@ -209,20 +210,22 @@ static int load_state(heat_ctx *c, const double *src, int64_t n, cudaMemcpyKind 
     rc = heat::convert_f64_to_state(c, src, dst, n);
     if (rc != HEAT_OK) return rc;
   } else {
-    // binary64 input does not fit the binary32 buffers: stage it through a
-    // transient device chunk and round each chunk on the device
-    double *stage = nullptr;
-    const int64_t chunk = n < kStageElems ? n : kStageElems;
-    if (cudaMalloc((void **)&stage, (size_t)chunk * sizeof(double)) != cudaSuccess) return HEAT_ENOMEM;
-    for (int64_t off = 0; off < n && rc == HEAT_OK; off += chunk) {
-      const int64_t m = n - off < chunk ? n - off : chunk;
+    // binary64 input does not fit the binary32 buffers: stage it through two
+    // device chunks used in turn and round each chunk on the device; stream
+    // order keeps a chunk's next copy behind its conversion
+    if (!c->xstage && cudaMalloc((void **)&c->xstage, 2 * (size_t)kStageElems * sizeof(double)) != cudaSuccess)
+      return HEAT_ENOMEM;
+    int64_t i = 0;
+    for (int64_t off = 0; off < n && rc == HEAT_OK; off += kStageElems, ++i) {
+      const int64_t m = n - off < kStageElems ? n - off : kStageElems;
+      double *stage = c->xstage + (i & 1) * kStageElems;
       if (cudaMemcpyAsync(stage, src + off, (size_t)m * sizeof(double), kind, c->stream) != cudaSuccess) rc = HEAT_ECUDA;
       if (rc == HEAT_OK) rc = heat::convert_f64_to_state(c, stage, (float *)dst + off, m);
-      if (rc == HEAT_OK && cudaStreamSynchronize(c->stream) != cudaSuccess) rc = HEAT_ECUDA;
     }
-    cudaStreamSynchronize(c->stream);
-    cudaFree(stage);
-    if (rc != HEAT_OK) return rc;
+    if (rc != HEAT_OK) {
+      cudaStreamSynchronize(c->stream);
+      return rc;
+    }
   }
   c->steps = 0;
   return HEAT_OK;
@@ -250,19 +253,21 @@ static int store_state(heat_ctx *c, double *dst, int64_t n, cudaMemcpyKind kind)
     rc = heat::convert_state_to_f64(c, src, dst, n);
     if (rc != HEAT_OK) return rc;
   } else {
-    double *stage = nullptr;
-    const int64_t chunk = n < kStageElems ? n : kStageElems;
-    if (cudaMalloc((void **)&stage, (size_t)chunk * sizeof(double)) != cudaSuccess) return HEAT_ENOMEM;
-    for (int64_t off = 0; off < n && rc == HEAT_OK; off += chunk) {
-      const int64_t m = n - off < chunk ? n - off : chunk;
+    // widen chunk by chunk into two device staging chunks used in turn
+    if (!c->xstage && cudaMalloc((void **)&c->xstage, 2 * (size_t)kStageElems * sizeof(double)) != cudaSuccess)
+      return HEAT_ENOMEM;
+    int64_t i = 0;
+    for (int64_t off = 0; off < n && rc == HEAT_OK; off += kStageElems, ++i) {
+      const int64_t m = n - off < kStageElems ? n - off : kStageElems;
+      double *stage = c->xstage + (i & 1) * kStageElems;
       rc = heat::convert_state_to_f64(c, (const float *)src + off, stage, m);
       if (rc == HEAT_OK && cudaMemcpyAsync(dst + off, stage, (size_t)m * sizeof(double), kind, c->stream) != cudaSuccess)
         rc = HEAT_ECUDA;
-      if (rc == HEAT_OK && cudaStreamSynchronize(c->stream) != cudaSuccess) rc = HEAT_ECUDA;
     }
-    cudaStreamSynchronize(c->stream);
-    cudaFree(stage);
-    if (rc != HEAT_OK) return rc;
+    if (rc != HEAT_OK) {
+      cudaStreamSynchronize(c->stream);
+      return rc;
+    }
   }
   return cudaStreamSynchronize(c->stream) == cudaSuccess ? HEAT_OK : HEAT_ECUDA;
 }

@@ -90,6 +90,7 @@ struct heat_ctx {
   double *partials;              // reduction scratch, device
   unsigned long long *tile_counter;  // dynamic tile counter of the temporal-blocking form, device
   double *hsum;                  // pinned host word for heat_sum
+  double *xstage;                // HEAT_F32C host transfers: two binary64 staging chunks (lazy)
   int64_t wait_ns;
   int32_t inj_segment;
   int64_t inj_step;
