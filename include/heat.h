@@ -154,8 +154,8 @@ int heat_set_stream(heat_ctx *c, void *cuda_stream);
 /* Select the kernel form and, for the blocked forms (HEAT_FORM_TBLOCK,
  * HEAT_FORM_CLUSTER, HEAT_FORM_PERSIST_TB), the temporal block depth T (1..64;
  * 0 = library default: 32 for HEAT_F32C; for HEAT_F64 8, except in the
- * temporal-blocking form on rings of at least 2^22 points: 12 when part of the
- * tiles run on the integer pipes, 4 when every tile runs on the FP64 unit).
+ * temporal-blocking form: 12 when part of the tiles run on the integer pipes,
+ * 4 on rings of at least 2^22 points when every tile runs on the FP64 unit).
  * T is ignored by the one-step forms.  HEAT_FORM_AUTO (the
  * default) is HEAT_FORM_CLUSTER for rings that one thread-block cluster holds,
  * else HEAT_FORM_TBLOCK. */

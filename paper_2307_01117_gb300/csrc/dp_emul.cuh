@@ -312,11 +312,13 @@ HEAT_HD X eq2x(X ul, X u, X ur, const MulX &r) {
 // Screening bounds for T steps with multiplier r (normal, nonzero); false when
 // no input passes.  Every value the steps produce is an integer multiple of
 // the inputs' granularity g = 2^(emin - 52), shrunk by at most 2^(52 - e_r)
-// per step through the product, so a nonzero result is at least
-// g * 2^(-T (52 - e_r)); magnitudes grow at most by (1 + 4|r|) per step.
+// per step through the rounded product (by exactly 2^e_r when r = +-2^e_r,
+// whose products are exact), so a nonzero result is at least
+// g * 2^(-T * shrink); magnitudes grow at most by (1 + 4|r|) per step.
 HEAT_HD bool domain_bounds(uint64_t r, int T, int &lo, int &hi) {
   const int er = (int)((r & kAbs) >> 52) - 1023;  // |r| in [2^er, 2^(er+1))
-  const int shrink = er < 52 ? 52 - er : 0;
+  const bool pow2 = (r & kFrac) == 0;
+  const int shrink = pow2 ? (er < 0 ? -er : 0) : (er < 52 ? 52 - er : 0);
   lo = 53 + T * shrink + 3;
   // ceil(log2(1 + 4|r|)) <= max(er + 3, 0) + 1
   const int grow = (er + 3 > 0 ? er + 3 : 0) + 1;

@@ -384,16 +384,16 @@ unsigned tblock_emul_mask(const heat_ctx *c) {
   return emul_share_mask(emul_auto_share(c->r));
 }
 
-// Default depth: binary32 pairs 32 steps per pass; binary64 8 (fewer launches
-// and ghost trips: +16 % to +47 % over T = 4 on rings of 2^16 to 2^19 points),
-// 12 on rings of at least 2^22 points with integer tiles (the integer tiles
-// unpack and pack once per pass: +1.3 % over 8 at 2^28 points), and 4 on such
-// rings with every tile on the FP64 unit (the halo's redundant work then costs
-// more than it saves: 129.1 vs 127.4 GLUP/s at 2^28 points).
+// Default depth: binary32 pairs 32 steps per pass; binary64 12 with integer
+// tiles (they unpack and pack once per pass: +13 % over 8 at 10^6 points,
+// +1.3 % at 2^28), else 8 (fewer launches and ghost trips: +16 % to +47 % over
+// T = 4 on rings of 2^16 to 2^19 points), except 4 on rings of at least 2^22
+// points (the halo's redundant work then costs more than it saves: 129.1 vs
+// 127.4 GLUP/s at 2^28 points).
 int tblock_default_T(const heat_ctx *c) {
   if (c->dtype == HEAT_F32C) return 32;
-  if (c->geo.N < (1LL << 22)) return 8;
-  return tblock_emul_mask(c) ? 12 : 4;
+  if (tblock_emul_mask(c)) return 12;
+  return c->geo.N < (1LL << 22) ? 8 : 4;
 }
 
 int run_tblock(heat_ctx *c, int64_t nt) {

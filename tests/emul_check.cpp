@@ -176,12 +176,14 @@ int main(int argc, char **argv) {
   // whole tiles: smooth, random, integer-valued (zero second differences), near
   // the screen's lower bound, mixed magnitudes; several r and T
   const double rs[] = {0.25, 0.5, 0.3, 0.123456789, 1e-3, -0.3, 2.0, 0.4999};
-  const int Ts[] = {1, 4, 8, 12};
+  const int Ts[] = {1, 4, 8, 12, 24, 40};
   for (long i = 0; i < std::max(1L, n / 2000); ++i) {
     for (double r : rs) {
       for (int T : Ts) {
         int lo = 0, hi = 0;
         if (!domain_bounds(bits(r), T, lo, hi)) continue;
+        // deep blocks: r = 2^k only (for other r the screen then excludes ordinary data)
+        if (T > 12 && (bits(r) & 0x000fffffffffffffull) != 0) continue;
         std::vector<double> a(64), b(64), c(64), d(64), f(64);
         const double base = U(g);
         for (int k = 0; k < 64; ++k) {
