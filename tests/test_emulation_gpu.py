@@ -126,3 +126,17 @@ def test_power_of_two_r_fp64_tiles(r, share):
     u0[5000:5004] = 2e-310
     u0[7000:7010] = 1e-250
     assert np.array_equal(bits(run(u0, r, 29, 8, share)), bits(oracle.run(u0, r, 29)))
+
+
+@pytest.mark.parametrize("k", [0.3, 0.25])
+def test_two_engine_split_on_a_large_ring_is_bitwise_the_oracle(k):
+    """The library's default on 2^22 points (adaptive split between the FP64
+    unit and the integer pipes, depth 12, three blocks and a partial one),
+    element by element against the oracle."""
+    n = 1 << 22
+    u0 = workloads.uniform_plus_mode(n, seed=11, m=5)
+    with H.Heat(n // 8, 8, k, 1.0, 1.0) as h:
+        got = h.set(u0).run(40).get()
+        assert H.heat_get_emulation(h.ctx) == -1
+        assert H.heat_last_run(h.ctx)["T"] == 12
+    assert np.array_equal(bits(got), bits(oracle.run(u0, k, 40)))
