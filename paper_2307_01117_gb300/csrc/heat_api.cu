@@ -61,6 +61,11 @@ int sync_status(heat_ctx *c) {
 
 int reset_status(heat_ctx *c) {
   c->host_error = HEAT_OK;
+  // the temporal-blocking counters too (a launch cut short by an error may have
+  // left them nonzero)
+  c->counter_dirty = 0;
+  if (cudaMemsetAsync(c->tile_counter, 0, 2 * sizeof(unsigned long long), c->stream) != cudaSuccess)
+    return HEAT_ECUDA;
   return heat::cuda_status(cudaMemsetAsync(c->dstat, 0, sizeof(DevStatus), c->stream));
 }
 
@@ -178,8 +183,10 @@ int heat_create(heat_ctx **out, int64_t nx, int32_t np, double k, double dt, dou
   if (rc == HEAT_OK && cudaMalloc((void **)&c->partials, sizeof(double) * (heat::kSumBlocks + 1)) != cudaSuccess)
     rc = HEAT_ENOMEM;
   if (rc == HEAT_OK && cudaMallocHost((void **)&c->hsum, sizeof(double)) != cudaSuccess) rc = HEAT_ENOMEM;
-  if (rc == HEAT_OK && cudaMalloc((void **)&c->tile_counter, sizeof(unsigned long long)) != cudaSuccess)
+  if (rc == HEAT_OK && cudaMalloc((void **)&c->tile_counter, 2 * sizeof(unsigned long long)) != cudaSuccess)
     rc = HEAT_ENOMEM;
+  if (rc == HEAT_OK && cudaMemsetAsync(c->tile_counter, 0, 2 * sizeof(unsigned long long), c->stream) != cudaSuccess)
+    rc = HEAT_ECUDA;
   if (rc == HEAT_OK) {
     for (int i = 0; i < 2 && rc == HEAT_OK; ++i)
       if (cudaMemsetAsync(c->buf[i], 0, (size_t)N * elem, c->stream) != cudaSuccess) rc = HEAT_ECUDA;
@@ -287,10 +294,14 @@ int heat_run(heat_ctx *c, int64_t nt) {
   int form = c->form;
   // default: one cluster launch for small rings (latency-bound: one launch for
   // all steps, ghost exchange through distributed shared memory), temporal
-  // blocking otherwise (the fastest form measured for both dtypes)
+  // blocking otherwise.  Binary64 switches at 6144 points: above, the
+  // temporal-blocking launches (graph-replayed, depth 24) are faster than one
+  // cluster's 16 SMs (0.67 vs 1.1 us per step at 8192 points; 0.56 vs 0.67
+  // for the cluster at 4000).
   if (form == HEAT_FORM_AUTO) {
     const int Tc = c->T > 0 ? c->T : (c->dtype == HEAT_F32C ? 32 : 8);
-    form = c->geo.N <= heat::cluster_max_points(c, Tc) ? HEAT_FORM_CLUSTER : HEAT_FORM_TBLOCK;
+    const int64_t limit = c->dtype == HEAT_F32C ? heat::cluster_max_points(c, Tc) : 6144;
+    form = c->geo.N <= limit && c->geo.N <= heat::cluster_max_points(c, Tc) ? HEAT_FORM_CLUSTER : HEAT_FORM_TBLOCK;
   }
   c->last_form = form;
   c->last_T = 1;

@@ -88,7 +88,8 @@ struct heat_ctx {
   int graph_last_T;
   int64_t graph_last_launches;
   double *partials;              // reduction scratch, device
-  unsigned long long *tile_counter;  // dynamic tile counter of the temporal-blocking form, device
+  unsigned long long *tile_counter;  // temporal-blocking form, device: [0] tile counter, [1] finished CTAs
+  int counter_dirty;             // a strided launch left tile_counter[0] nonzero
   double *hsum;                  // pinned host word for heat_sum
   double *xstage;                // HEAT_F32C host transfers: two binary64 staging chunks (lazy)
   int64_t wait_ns;

@@ -52,7 +52,7 @@ struct TBArgs {
   int64_t ntiles;
   DevStatus *st;
   unsigned emul_mask;  // bit (tile mod 32) set: compute the tile on the integer pipes
-  unsigned long long *tile_counter;  // launch-wide tile counter, zero at launch
+  unsigned long long *tile_counter;  // [0] launch-wide tile counter (zero at launch), [1] finished CTAs
   int split;           // other tiles: multiply (and masked final adds) on the integer pipes
   unsigned add_mask;   // registers k whose final add also goes to the integer pipes
   emul::Mul m;         // prepared multiplier r (valid when emul_mask != 0)
@@ -259,6 +259,18 @@ __global__ void __launch_bounds__(kWarps * 32, MODE == 2 ? 1 : 8) k_tblock_c(TBA
       if (i >= a.T && i < WIN - a.T && g < N) dst[g] = P::store(R, k);
     }
   }
+  // The last CTA to finish returns both counters to zero for the next launch
+  // on the stream, so launches need no reset operation between them (on small
+  // rings the launch sequence is the cost).  Every warp has made its last claim
+  // before its CTA passes the barrier.
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(a.tile_counter + 1, 1ull) == (unsigned long long)gridDim.x - 1) {
+      atomicExch(a.tile_counter, 0ull);
+      atomicExch(a.tile_counter + 1, 0ull);
+    }
+  }
 }
 
 template <int MODE, int EP>
@@ -273,7 +285,13 @@ int launch_tb_c_ep(heat_ctx *c, TBArgs a) {
   const int64_t cap = (int64_t)per_sm * c->sms;
   if (grid > cap) grid = cap;
   if (grid < 1) grid = 1;
-  if (cudaMemsetAsync(c->tile_counter, 0, sizeof(unsigned long long), c->stream) != cudaSuccess) return HEAT_ECUDA;
+  // zero after the previous launch (k_tblock_c resets them itself), unless a
+  // strided launch ran since
+  if (c->counter_dirty) {
+    if (cudaMemsetAsync(c->tile_counter, 0, 2 * sizeof(unsigned long long), c->stream) != cudaSuccess)
+      return HEAT_ECUDA;
+    c->counter_dirty = 0;
+  }
   k_tblock_c<MODE, EP><<<(int)grid, kWarps * 32, 0, c->stream>>>(a);
   return cuda_status(cudaGetLastError());
 }
@@ -362,6 +380,7 @@ int launch_tb(heat_ctx *c, const void *src, void *dst, int T, int steps) {
   if (grid > cap) grid = cap;
   if (grid < 1) grid = 1;
   if (cudaMemsetAsync(c->tile_counter, 0, sizeof(unsigned long long), c->stream) != cudaSuccess) return HEAT_ECUDA;
+  c->counter_dirty = 1;
   k_tblock<MODE><<<(int)grid, kWarps * 32, smem, c->stream>>>(a);
   return cuda_status(cudaGetLastError());
 }
@@ -384,14 +403,16 @@ unsigned tblock_emul_mask(const heat_ctx *c) {
   return emul_share_mask(emul_auto_share(c->r));
 }
 
-// Default depth: binary32 pairs 32 steps per pass; binary64 12 with integer
-// tiles (they unpack and pack once per pass: +13 % over 8 at 10^6 points,
-// +1.3 % at 2^28), else 8 (fewer launches and ghost trips: +16 % to +47 % over
-// T = 4 on rings of 2^16 to 2^19 points), except 4 on rings of at least 2^22
-// points (the halo's redundant work then costs more than it saves: 129.1 vs
-// 127.4 GLUP/s at 2^28 points).
+// Default depth: binary32 pairs 32 steps per pass.  Binary64: 24 on rings
+// below 2^19 points, where the launch sequence is the cost (0.67 us per step
+// against 0.82 at T = 12 and 1.24 at T = 8 from 4000 to 31000 points; +8 % at
+// 2^18); 12 with integer tiles (they unpack and pack once per pass: +13 % over
+// 8 at 10^6 points, +1.3 % at 2^28); else 8, except 4 on rings of at least
+// 2^22 points (the halo's redundant work then costs more than it saves: 129.1
+// vs 127.4 GLUP/s at 2^28 points).
 int tblock_default_T(const heat_ctx *c) {
   if (c->dtype == HEAT_F32C) return 32;
+  if (c->geo.N < (1LL << 19)) return 24;
   if (tblock_emul_mask(c)) return 12;
   return c->geo.N < (1LL << 22) ? 8 : 4;
 }

@@ -79,10 +79,17 @@ def test_cluster_rejects_rings_beyond_its_limit():
 
 
 def test_auto_picks_cluster_for_small_rings():
+    """Binary64: the cluster form up to 6144 points, temporal blocking above
+    (depth 24 below 2^19 points); binary32: the cluster form while one cluster
+    holds the ring."""
     with H.Heat(1000, 4, 0.5, 1.0, 1.0) as h:
         h.set(workloads.ramp(4000)).run(10)
         assert H.heat_last_run(h.ctx)["form"] == "cluster"
     with H.Heat(30000, 1, 0.5, 1.0, 1.0) as h:
+        h.set(np.zeros(30000)).run(10)
+        last = H.heat_last_run(h.ctx)
+        assert last["form"] == "tblock" and last["T"] == 24
+    with H.Heat(30000, 1, 0.5, 1.0, 1.0, dtype="f32c") as h:
         h.set(np.zeros(30000)).run(10)
         assert H.heat_last_run(h.ctx)["form"] == "cluster"
     with H.Heat(100000, 1, 0.5, 1.0, 1.0) as h:

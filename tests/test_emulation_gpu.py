@@ -107,7 +107,7 @@ def test_automatic_share_is_resolved_per_ring_and_exact():
     with H.Heat(40000, 1, 0.25, 1.0, 1.0, form="tblock") as h:
         assert H.heat_get_emulation(h.ctx) == 0
         h.set(workloads.uniform(40000, 6, -1, 1)).run(9)
-        assert H.heat_last_run(h.ctx)["T"] == 8
+        assert H.heat_last_run(h.ctx)["T"] == 24           # small ring: launch-bound
     with pytest.raises(H.HeatError):
         with H.Heat(100, 1, 0.25, 1.0, 1.0) as h:
             H.heat_set_emulation(h.ctx, -2)
