@@ -299,7 +299,7 @@ int heat_run(heat_ctx *c, int64_t nt) {
   // cluster's 16 SMs (0.67 vs 1.1 us per step at 8192 points; 0.56 vs 0.67
   // for the cluster at 4000).
   if (form == HEAT_FORM_AUTO) {
-    const int Tc = c->T > 0 ? c->T : (c->dtype == HEAT_F32C ? 32 : 8);
+    const int Tc = c->T > 0 ? c->T : (c->dtype == HEAT_F32C ? 32 : 16);
     const int64_t limit = c->dtype == HEAT_F32C ? heat::cluster_max_points(c, Tc) : 6144;
     form = c->geo.N <= limit && c->geo.N <= heat::cluster_max_points(c, Tc) ? HEAT_FORM_CLUSTER : HEAT_FORM_TBLOCK;
   }

@@ -202,8 +202,11 @@ int64_t cluster_max_points(const heat_ctx *c, int T) {
 
 int run_cluster(heat_ctx *c, int64_t nt) {
   const int mode = c->dtype == HEAT_F32C ? 2 : (c->arith == HEAT_ARITH_FMA ? 1 : 0);
-  const int T = c->T > 0 ? c->T : (c->dtype == HEAT_F32C ? 32 : 8);
   const int64_t N = c->geo.N;
+  // default depth: binary32 32; binary64 16 (0.53 vs 0.59 us per step at 4000
+  // points), or 8 for rings that only fit at that depth
+  const int T = c->T > 0 ? c->T
+                         : (c->dtype == HEAT_F32C ? 32 : (N <= cluster_max_points(c, 16) ? 16 : 8));
   const int *eps = c->dtype == HEAT_F32C ? kEp32 : kEp64;
   if (2 * T >= 32 * eps[2]) return HEAT_EINVAL;
   if (N > cluster_max_points(c, T)) return HEAT_ENOTSUP;
