@@ -8,6 +8,7 @@
 #include <nvtx3/nvToolsExt.h>
 #include <stdio.h>
 
+#include "dp_emul.cuh"
 #include "heat_internal.cuh"
 
 using heat::DevStatus;
@@ -386,7 +387,14 @@ int heat_set_emulation(heat_ctx *c, int share) {
 
 int heat_get_emulation(const heat_ctx *c, int *share) {
   if (!c || !share) return HEAT_EINVAL;
-  const unsigned mask = heat::tblock_emul_mask(c);
+  unsigned mask = heat::tblock_emul_mask(c);
+  // integer tiles need a screen that admits values at the depth in use (the
+  // contiguous layout; the strided layout checks per operation instead)
+  uint64_t rb;
+  memcpy(&rb, &c->r, sizeof(rb));
+  int lo = 0, hi = 0;
+  const int T = c->T > 0 ? c->T : heat::tblock_default_T(c);
+  if (c->tb_layout == 1 && !heat::emul::domain_bounds(rb, T, lo, hi)) mask = 0u;
   // the library's choice is adaptive (two-ended tile claiming): reported as -1
   *share = c->emul_auto && mask ? -1 : __builtin_popcount(mask);
   return HEAT_OK;

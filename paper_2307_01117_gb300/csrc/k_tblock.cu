@@ -412,8 +412,13 @@ unsigned tblock_emul_mask(const heat_ctx *c) {
 // vs 127.4 GLUP/s at 2^28 points).
 int tblock_default_T(const heat_ctx *c) {
   if (c->dtype == HEAT_F32C) return 32;
-  if (c->geo.N < (1LL << 19)) return 24;
-  if (tblock_emul_mask(c)) return 12;
+  const bool int_tiles = tblock_emul_mask(c) != 0u;
+  uint64_t rb;
+  memcpy(&rb, &c->r, sizeof(rb));
+  // a general r's screen admits ordinary data only for shallow blocks: keep
+  // the integer tiles at 12 rather than lose them at 24
+  if (c->geo.N < (1LL << 19) && !(int_tiles && (rb & 0x000fffffffffffffull) != 0)) return 24;
+  if (int_tiles) return 12;
   return c->geo.N < (1LL << 22) ? 8 : 4;
 }
 
