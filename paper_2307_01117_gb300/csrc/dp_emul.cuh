@@ -253,15 +253,15 @@ HEAT_HD X add(X x, X y) {
 
 // A multiplier r (normal, nonzero) prepared for the unpacked form.
 struct MulX {
-  uint64_t sig11;  // significand with its leading 1 at bit 63
-  int e;           // r = sig * 2^e with sig in [2^52, 2^53)
+  int64_t sig10;   // significand (in [2^52, 2^53)) shifted left by 10: in [2^62, 2^63)
+  int e;           // r = sig * 2^e
   bool neg;
   bool pow2;       // r = +-2^k: the product only moves the exponent
 };
 
 HEAT_HD MulX prepare_mulx(uint64_t r) {
   MulX m;
-  m.sig11 = ((r & kFrac) | kImpl) << 11;
+  m.sig10 = (int64_t)(((r & kFrac) | kImpl) << 10);
   m.e = (int)((r & kAbs) >> 52) - 1075;
   m.neg = (r >> 63) != 0;
   m.pow2 = (r & kFrac) == 0;
@@ -277,22 +277,34 @@ HEAT_HD X scale(X x, const MulX &r) {
   return y;
 }
 
-// r * x, rounded to nearest-even: |m| * 2^3 times r's significand * 2^11 is a
-// 128-bit product in [2^125, 2^127); its high word, normalised to a leading 1 at
-// bit 62 with the remaining bits as a sticky bit, is rounded at bit 10 and
-// moved to bit 59.
+HEAT_HD int64_t mulhi_s64(int64_t a, int64_t b) {
+#if defined(__CUDA_ARCH__)
+  return __mul64hi(a, b);
+#else
+  return (int64_t)(((__int128)a * b) >> 64);
+#endif
+}
+
+// |r| * x, rounded to nearest-even, on the signed value: (m * 2^2) * (sig *
+// 2^10) is a two's complement 128-bit product P with |P| in [2^123, 2^125).
+// Its high word V = floor(P / 2^64) has the leading bit of |P| at bit 59 or
+// 60 (found on the one's complement, as in add), so the 53 kept bits end at
+// bit q = 7 or 8; V is rounded at q by floor((V + 2^(q-1) - 1 + (s | bit_q)) /
+// 2^q) * 2^q with s = (low word != 0) -- round to nearest-even for two's
+// complement values with the low word as the discarded fraction -- and shifted
+// to a leading bit at 59.  A negative r negates the rounded result (rounding to
+// nearest is symmetric).
 HEAT_HD X mul(X x, const MulX &r) {
-  const bool xn = x.m < 0;
-  const uint64_t a = (uint64_t)(xn ? -x.m : x.m) << 3;
-  const uint64_t hi = mulhi64(a, r.sig11);
-  const uint64_t lo = a * r.sig11;
-  const int top = (int)(hi >> 62);  // 1: leading 1 at bit 62; 0: at bit 61 (or x = 0)
-  uint64_t s = top ? hi : ((hi << 1) | (lo >> 63));
-  const uint64_t rest = top ? lo : (lo << 1);
-  s |= (uint64_t)(rest != 0);
-  const uint64_t q = ((s + 511 + ((s >> 10) & 1)) & ~1023ull) >> 3;
+  const int64_t a = (int64_t)((uint64_t)x.m << 2);
+  const int64_t V = mulhi_s64(a, r.sig10);
+  const uint64_t lo = (uint64_t)a * (uint64_t)r.sig10;
+  const int top = (int)(((uint64_t)(V ^ (V >> 63)) >> 60) & 1);  // leading bit at 60 (1) or 59 (0)
+  const int q = 7 + top;
+  const int64_t inc = ((int64_t)1 << (q - 1)) - 1 + (int64_t)((lo != 0) | ((V >> q) & 1));
+  const int64_t R = (V + inc) & ~(((int64_t)1 << q) - 1);
   X y;
-  y.m = (xn != r.neg) ? -(int64_t)q : (int64_t)q;
+  y.m = R >> top;
+  if (r.neg) y.m = -y.m;
   y.e = x.e + r.e + 52 + top;
   y.pad = 0;
   return y;

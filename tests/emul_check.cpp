@@ -172,6 +172,15 @@ int main(int argc, char **argv) {
     check_mulx(xe, 3.0, 1.0 / 3.0);
     check_mulx(xe, -3.0, 1.0 / 3.0);
     check_mulx(xe, std::nextafter(2.0, 0.0), std::nextafter(2.0, 0.0));
+    // exact ties of the product (the discarded part is exactly half an ulp), both signs
+    const double u52 = std::ldexp(1.0, -52);
+    const double tie_x[] = {1.0 + u52, 1.0 + 3 * u52, 1.0 + 5 * u52, 2.0 - u52};
+    const double tie_r[] = {3.0, 1.5, 0.75, -3.0, -1.5};
+    for (double xv : tie_x)
+      for (double rv : tie_r) {
+        check_mulx(xe, rv, xv);
+        check_mulx(xe, rv, -xv);
+      }
   }
   // whole tiles: smooth, random, integer-valued (zero second differences), near
   // the screen's lower bound, mixed magnitudes; several r and T
