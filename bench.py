@@ -22,8 +22,10 @@ steps, take the FP64 conservation sum (single ring) or synchronise (batch).
 value = ring point-steps / second (GLUP/s, the paper's "cells processed per
 second", Section 6), timed with CUDA events on the work's stream, 3+ warm-ups,
 inputs larger than L2.  `e2e` is the same metric through the C ABI with host
-buffers: the initial state is copied in from pinned host memory and the final
-state read back inside the timed region.  `cpu_baseline` is the CPU oracle,
+buffers: every step's initial state is copied in from pinned host memory and
+its final state read back inside the timed region (single rings: two contexts
+on two streams take the steps in turn, so one context's copies run while the
+other advances its ring).  `cpu_baseline` is the CPU oracle,
 single-threaded, on a bounded sample; `cpu_threaded` is the paper's parallel
 algorithm (one host thread per segment, SPSC ghost queues) on every host core,
 on the same sample.
@@ -325,9 +327,10 @@ def run_reference(args, w: dict, rank: int) -> None:
 
 
 # ---------------------------------------------------------------------------------------------
-# Runners, one per workload kind: step(events), e2e_prepare/e2e_step, kernel_info, config.
+# Runners, one per workload kind: step(events), e2e_prepare/e2e_run, kernel_info, config.
 
 class RingRunner:
+    E2E_COPIES = "beside the steps: two contexts on two streams take the steps in turn"
     def __init__(self, args, w, H, torch, local, stream):
         self.args, self.w, self.H, self.torch, self.stream = args, w, H, torch, stream
         self.n = w["nx"] * w["np"]
@@ -335,15 +338,21 @@ class RingRunner:
         self.point_steps = float(self.n) * self.nt
         self.u0 = initial_state(w)
         self.u0_dev = torch.from_numpy(self.u0).to(f"cuda:{local}")
+        self.h = self._context(stream)
+        self.h2 = None
+
+    def _context(self, stream):
+        args, w, H = self.args, self.w, self.H
         arith = H.HEAT_ARITH_FMA if args.arith == "fma" else H.HEAT_ARITH_EXACT
-        self.h = H.Heat(w["nx"], w["np"], w["k"], w["dt"], w["dx"], dtype=w["dtype"], form=args.form, T=args.T,
-                        arith=arith, stream=stream)
+        h = H.Heat(w["nx"], w["np"], w["k"], w["dt"], w["dx"], dtype=w["dtype"], form=args.form, T=args.T,
+                   arith=arith, stream=stream)
         if args.layout >= 0:
-            H.heat_set_layout(self.h.ctx, args.layout)
+            H.heat_set_layout(h.ctx, args.layout)
         if args.split:
-            H.heat_set_split(self.h.ctx, args.split)
+            H.heat_set_split(h.ctx, args.split)
         if args.emul >= 0:
-            H.heat_set_emulation(self.h.ctx, args.emul)
+            H.heat_set_emulation(h.ctx, args.emul)
+        return h
 
     def step(self, ev=None):
         H, ctx = self.H, self.h.ctx
@@ -356,17 +365,43 @@ class RingRunner:
         H.heat_sum(ctx)  # synchronises the stream
 
     def e2e_prepare(self):
+        # two contexts on two streams take the steps in turn: while one advances
+        # its ring, the other's result is read back and its next input copied
+        # in; an event keeps the two contexts' steps in order on the device
         torch = self.torch
         self.host_in = torch.empty(self.n, dtype=torch.float64, pin_memory=True).numpy()
         self.host_in[:] = self.u0
-        self.host_out = torch.empty(self.n, dtype=torch.float64, pin_memory=True).numpy()
+        self.host_out = [torch.empty(self.n, dtype=torch.float64, pin_memory=True).numpy() for _ in range(2)]
+        if self.h2 is None:
+            self.stream2 = torch.cuda.Stream()
+            self.h2 = self._context(self.stream2)
+        self.pipe = [(self.h, self.stream), (self.h2, self.stream2)]
+        self.done = [torch.cuda.Event(), torch.cuda.Event()]
 
-    def e2e_step(self):
-        H, ctx = self.H, self.h.ctx
-        H.heat_set(ctx, self.host_in)
-        H.heat_run(ctx, self.nt)
-        H.heat_sum(ctx)
-        H.heat_get(ctx, self.host_out)
+    def e2e_run(self, k):
+        H, prev = self.H, None
+        for i in range(k):
+            x = i & 1
+            h, s = self.pipe[x]
+            H.heat_set(h.ctx, self.host_in)           # host -> device, beside the other context's steps
+            if prev is not None:
+                s.wait_event(self.done[prev])
+            H.heat_run(h.ctx, self.nt)
+            self.done[x].record(s)
+            if prev is not None:
+                self._e2e_finish(prev)                # device -> host, beside this context's steps
+            prev = x
+        self._e2e_finish(prev)
+
+    def e2e_agree(self):
+        """Both contexts advanced the same input: their read-back states agree bitwise."""
+        a, b = (o.view(np.uint64) for o in self.host_out)
+        return bool(np.array_equal(a, b))
+
+    def _e2e_finish(self, x):
+        ctx = self.pipe[x][0].ctx
+        self.H.heat_sum(ctx)
+        self.H.heat_get(ctx, self.host_out[x])
 
     def e2e_bytes(self):
         return self.n * 8, self.n * 8
@@ -412,9 +447,12 @@ class RingRunner:
 
     def close(self):
         self.h.close()
+        if self.h2 is not None:
+            self.h2.close()
 
 
 class BatchRunner:
+    E2E_COPIES = "in series with the steps"
     def __init__(self, args, w, H, torch, local, stream):
         from paper_2307_01117_gb300 import workloads
         self.args, self.w, self.H, self.torch, self.stream = args, w, H, torch, stream
@@ -452,7 +490,11 @@ class BatchRunner:
         self.host_in = [torch.from_numpy(u).pin_memory().numpy() for u in self.inits]
         self.host_out = [torch.empty(s.n, dtype=torch.float64, pin_memory=True).numpy() for s in self.specs]
 
-    def e2e_step(self):
+    def e2e_run(self, k):
+        for _ in range(k):
+            self._e2e_step()
+
+    def _e2e_step(self):
         H = self.H
         for rid in self.ids:
             H.heat_batch_remove(self.b, rid)
@@ -464,6 +506,9 @@ class BatchRunner:
 
     def e2e_bytes(self):
         return self.n_total * 8, self.n_total * 8
+
+    def e2e_agree(self):
+        return None
 
     def kernel_info(self, run_ms):
         T = self.tuned[0]
@@ -537,6 +582,7 @@ class PrecisionRunner(RingRunner):
 
 
 class ServeRunner:
+    E2E_COPIES = None
     """One step = one window of Poisson arrivals replayed in real time through the
     continuous-batching server (not drained at the window's end: unfinished
     requests count as backlog)."""
@@ -573,7 +619,7 @@ class ServeRunner:
     def e2e_prepare(self):
         pass
 
-    def e2e_step(self):
+    def e2e_run(self, k):
         pass
 
     def e2e_bytes(self):
@@ -750,17 +796,17 @@ def main() -> int:
     e2e = None
     if not args.no_e2e and w["kind"] != "serve":
         runner.e2e_prepare()
-        runner.e2e_step()
+        runner.e2e_run(2)
         barrier()
-        k_e2e = max(1, min(args.steps, 3))
+        k_e2e = max(1, min(args.steps, 5))
         t0 = time.perf_counter()
-        for _ in range(k_e2e):
-            runner.e2e_step()
+        runner.e2e_run(k_e2e)
         barrier()
         dt_e2e = max_over_ranks(time.perf_counter() - t0)
         bi, bo = runner.e2e_bytes()
         e2e = {"value": world * runner.point_steps * k_e2e / dt_e2e / 1e9, "unit": UNIT, "h2d_bytes_per_step": bi,
-               "d2h_bytes_per_step": bo, "steps": k_e2e}
+               "d2h_bytes_per_step": bo, "steps": k_e2e, "copies": runner.E2E_COPIES,
+               "contexts_agree_bitwise": runner.e2e_agree()}
 
     cb = ct = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and w["kind"] != "serve":

@@ -30,4 +30,6 @@ def test_bench_json_line_contract():
     assert rf["emul_share_of_32"] == d["config"]["emul_share_of_32"]
     e = d["e2e"]
     assert e["value"] > 0 and e["h2d_bytes_per_step"] == e["d2h_bytes_per_step"] == 8 * (1 << 25)
+    # copies run beside the other context's steps, never instead of them
+    assert e["value"] <= 1.1 * d["value"] and e["contexts_agree_bitwise"] is True
     assert d["gpu_launches"] > 0
