@@ -153,10 +153,13 @@ int heat_set_stream(heat_ctx *c, void *cuda_stream);
 
 /* Select the kernel form and, for the blocked forms (HEAT_FORM_TBLOCK,
  * HEAT_FORM_CLUSTER, HEAT_FORM_PERSIST_TB), the temporal block depth T (1..64;
- * 0 = library default: 32 for HEAT_F32C; for HEAT_F64 8, except in the
- * temporal-blocking form: 24 on rings below 2^19 points, 12 when part of the
- * tiles run on the integer pipes, 4 on rings of at least 2^22 points when every
- * tile runs on the FP64 unit).  T is ignored by the one-step forms.
+ * 0 = library default: 32 for HEAT_F32C; for HEAT_F64 in the temporal-blocking
+ * form 24 on rings below 2^19 points (12 there when integer tiles run at an r
+ * that is not a power of two), else 12 when part of the tiles run on the
+ * integer pipes, else 8 below 2^22 points and 4 from 2^22 points; in the
+ * cluster form 16, or 8 for rings that one cluster holds only at that depth;
+ * in the persistent temporal-blocking form 12).  T is ignored by the one-step
+ * forms.
  * HEAT_FORM_AUTO (the default) is HEAT_FORM_CLUSTER for binary64 rings of at
  * most 6144 points and binary32 rings that one thread-block cluster holds,
  * else HEAT_FORM_TBLOCK. */

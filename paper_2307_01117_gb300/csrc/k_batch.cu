@@ -1041,7 +1041,10 @@ int run_persist_tb(heat_ctx *c, int64_t nt) {
   b->arena[0] = c->buf[0];
   b->arena[1] = c->buf[1];
   b->wait_ns = c->wait_ns;
-  const int T = c->T > 0 ? c->T : (c->dtype == HEAT_F32C ? 32 : 8);
+  b->emul_share = c->emul_auto ? -1 : c->emul_share;  // heat_set_emulation applies here too
+  // default depth: 32 for binary32; 12 for binary64, the depth at which the
+  // integer tiles' screen still admits ordinary data for a general r
+  const int T = c->T > 0 ? c->T : (c->dtype == HEAT_F32C ? 32 : 12);
   const int win = c->dtype == HEAT_F32C ? 32 * tb::TBC<2>::E : 32 * tb::TBC<0>::E;
   if (2 * T >= win) return HEAT_EINVAL;
   heat_batch::Ring r;

@@ -140,3 +140,20 @@ def test_two_engine_split_on_a_large_ring_is_bitwise_the_oracle(k):
         assert H.heat_get_emulation(h.ctx) == -1
         assert H.heat_last_run(h.ctx)["T"] == 12
     assert np.array_equal(bits(got), bits(oracle.run(u0, k, 40)))
+
+
+@pytest.mark.parametrize("T", [0, 8])
+@pytest.mark.parametrize("share", [-1, 0, 16, 32])
+@pytest.mark.parametrize("r", [0.25, 0.3])
+def test_persistent_temporal_blocking_takes_the_share(share, r, T):
+    """heat_set_emulation reaches the persistent temporal-blocking form (one
+    batch launch for the ring); every share gives the oracle's bits, at the
+    default depth (12) and at 8."""
+    n = 5 * 4096 + 77
+    u0 = workloads.uniform(n, 40 + share, -1, 1)
+    u0[300:340] = 0.0
+    with H.Heat(n, 1, r, 1.0, 1.0, form="persist_tb", T=T) as h:
+        H.heat_set_emulation(h.ctx, share)
+        got = h.set(u0).run(37).get()
+        assert H.heat_last_run(h.ctx)["T"] == (T or 12)
+    assert np.array_equal(bits(got), bits(oracle.run(u0, r, 37)))
