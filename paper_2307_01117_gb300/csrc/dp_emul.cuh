@@ -236,10 +236,21 @@ HEAT_HD X add(X x, X y) {
   const int64_t A = sw ? y.m : x.m;
   const int64_t Bs = sw ? x.m : y.m;
   const int eb = sw ? y.e : x.e;
-  int sh = sw ? -d : d;
-  sh = sh < 63 ? sh : 63;
-  int64_t B = Bs >> sh;
-  B |= (int64_t)(((uint64_t)B << sh) != (uint64_t)Bs);  // sticky
+  const int sh = sw ? -d : d;
+#if defined(__CUDA_ARCH__)
+  // PTX clamps shift amounts above the register width (sh exceeds 2^24 against
+  // a +0 operand): Bs >> sh is then all sign bits and B << sh is 0, the same
+  // result as a shift by 63 with the sticky set
+  int64_t B;
+  asm("shr.s64 %0, %1, %2;" : "=l"(B) : "l"(Bs), "r"(sh));
+  uint64_t Bb;
+  asm("shl.b64 %0, %1, %2;" : "=l"(Bb) : "l"(B), "r"(sh));
+  B |= (int64_t)(Bb != (uint64_t)Bs);  // sticky
+#else
+  const int shc = sh < 63 ? sh : 63;
+  int64_t B = Bs >> shc;
+  B |= (int64_t)(((uint64_t)B << shc) != (uint64_t)Bs);  // sticky
+#endif
   const int64_t S = A + B;
   const int p = msb_signed(S);                           // -1 (S = 0) .. 61
   const int64_t Sn = (int64_t)((uint64_t)S << (61 - p));
@@ -299,9 +310,11 @@ HEAT_HD X mul(X x, const MulX &r) {
   const int64_t V = mulhi_s64(a, r.sig10);
   const uint64_t lo = (uint64_t)a * (uint64_t)r.sig10;
   const int top = (int)(((uint64_t)(V ^ (V >> 63)) >> 60) & 1);  // leading bit at 60 (1) or 59 (0)
-  const int q = 7 + top;
-  const int64_t inc = ((int64_t)1 << (q - 1)) - 1 + (int64_t)((lo != 0) | ((V >> q) & 1));
-  const int64_t R = (V + inc) & ~(((int64_t)1 << q) - 1);
+  // q = 7 + top: 2^(q-1) - 1 and the mask of bits q.. as selects of constants
+  const int64_t half_m1 = top ? 127 : 63;
+  const int64_t keep = top ? ~(int64_t)255 : ~(int64_t)127;
+  const int64_t inc = half_m1 + (int64_t)((lo != 0) | ((V >> (7 + top)) & 1));
+  const int64_t R = (V + inc) & keep;
   X y;
   y.m = R >> top;
   if (r.neg) y.m = -y.m;
