@@ -279,12 +279,19 @@ HEAT_HD MulX prepare_mulx(uint64_t r) {
   return m;
 }
 
-// r * x for r = +-2^k.
-HEAT_HD X scale(X x, const MulX &r) {
+// |r| * x for r = +-2^k.
+HEAT_HD X scale_mag(X x, const MulX &r) {
   X y;
-  y.m = r.neg ? -x.m : x.m;
+  y.m = x.m;
   y.e = x.e + r.e + 52;
   y.pad = 0;
+  return y;
+}
+
+// r * x for r = +-2^k.
+HEAT_HD X scale(X x, const MulX &r) {
+  X y = scale_mag(x, r);
+  if (r.neg) y.m = -y.m;
   return y;
 }
 
@@ -304,8 +311,8 @@ HEAT_HD int64_t mulhi_s64(int64_t a, int64_t b) {
 // 2^q) * 2^q with s = (low word != 0) -- round to nearest-even for two's
 // complement values with the low word as the discarded fraction -- and shifted
 // to a leading bit at 59.  A negative r negates the rounded result (rounding to
-// nearest is symmetric).
-HEAT_HD X mul(X x, const MulX &r) {
+// nearest is symmetric): mul below; mul_mag leaves the sign of r out.
+HEAT_HD X mul_mag(X x, const MulX &r) {
   const int64_t a = (int64_t)((uint64_t)x.m << 2);
   const int64_t V = mulhi_s64(a, r.sig10);
   const uint64_t lo = (uint64_t)a * (uint64_t)r.sig10;
@@ -317,21 +324,30 @@ HEAT_HD X mul(X x, const MulX &r) {
   const int64_t R = (V + inc) & keep;
   X y;
   y.m = R >> top;
-  if (r.neg) y.m = -y.m;
   y.e = x.e + r.e + 52 + top;
   y.pad = 0;
   return y;
 }
 
+HEAT_HD X mul(X x, const MulX &r) {
+  X y = mul_mag(x, r);
+  if (r.neg) y.m = -y.m;
+  return y;
+}
+
 // Eq. 2, exact reading, unpacked: u + r*((ul - 2u) + ur), each step rounded.
-template <bool POW2>
+// POW2: r = +-2^k; NEG: r < 0 (the sign is fixed at compile time so that a
+// step does not select it per point).
+template <bool POW2, bool NEG>
 HEAT_HD X eq2x(X ul, X u, X ur, const MulX &r) {
   X m2u;
   m2u.m = -u.m;  // -2u, exact
   m2u.e = u.e + 1;
   m2u.pad = 0;
   const X t2 = add(add(ul, m2u), ur);
-  return add(u, POW2 ? scale(t2, r) : mul(t2, r));
+  X p = POW2 ? scale_mag(t2, r) : mul_mag(t2, r);
+  if (NEG) p.m = -p.m;
+  return add(u, p);
 }
 
 // Screening bounds for T steps with multiplier r (normal, nonzero); false when

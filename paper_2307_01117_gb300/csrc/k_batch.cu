@@ -224,10 +224,14 @@ __global__ void __launch_bounds__(kBWarps * 32, MODE == 2 ? 3 : 6) k_batch(Batch
           if (__all_sync(0xffffffffu, ok)) {
             if (!int_tile)  // r = +-2^k on the FP64 unit: the product moves the exponent
               for (int s = 0; s < steps; ++s) P::step_p2(reg, R.p2_hi_add, R.p2_hi_xor);
+            else if (R.mx.pow2 && !R.mx.neg)
+              P::template steps_x<true, false>(reg, steps, R.mx);
             else if (R.mx.pow2)
-              P::template steps_x<true>(reg, steps, R.mx);
+              P::template steps_x<true, true>(reg, steps, R.mx);
+            else if (!R.mx.neg)
+              P::template steps_x<false, false>(reg, steps, R.mx);
             else
-              P::template steps_x<false>(reg, steps, R.mx);
+              P::template steps_x<false, true>(reg, steps, R.mx);
             dp = false;
           }
         }

@@ -242,10 +242,14 @@ __global__ void __launch_bounds__(kWarps * 32, MODE == 2 ? 1 : 8) k_tblock_c(TBA
         if (__all_sync(kFull, ok)) {  // else the whole tile takes the plain FP64-unit steps
           if (!int_tile)
             for (int s = 0; s < a.steps; ++s) P::step_p2(R, a.p2_hi_add, a.p2_hi_xor);
+          else if (a.mx.pow2 && !a.mx.neg)
+            P::template steps_x<true, false>(R, a.steps, a.mx);
           else if (a.mx.pow2)
-            P::template steps_x<true>(R, a.steps, a.mx);
+            P::template steps_x<true, true>(R, a.steps, a.mx);
+          else if (!a.mx.neg)
+            P::template steps_x<false, false>(R, a.steps, a.mx);
           else
-            P::template steps_x<false>(R, a.steps, a.mx);
+            P::template steps_x<false, true>(R, a.steps, a.mx);
           dp = false;
         }
       }

@@ -224,11 +224,12 @@ struct TBCx<0, EP> : TBCf64<0, EP> {
   }
 
   // All `steps` steps of a tile on the integer pipes, in the unpacked form of
-  // dp_emul.cuh (the caller has screened the tile's values with in_domain).
+  // dp_emul.cuh (the caller has screened the tile's values with in_domain;
+  // POW2 and NEG must match m).
   // The lane's points live in a small local array (w[1..E], halo values in
   // w[0] and w[E+1]) walked by a loop that is not unrolled, which keeps the
   // code small enough for the instruction cache beside the FP64-unit tiles.
-  template <bool POW2>
+  template <bool POW2, bool NEG>
   static __device__ __forceinline__ void steps_x(typename TBCf64<0, EP>::Reg &R, int steps, const emul::MulX &m) {
     constexpr int E = EP;
     emul::X w[E + 2];
@@ -241,7 +242,7 @@ struct TBCx<0, EP> : TBCf64<0, EP> {
 #pragma unroll 4
       for (int k = 1; k <= E; ++k) {
         const emul::X nxt = w[k + 1];
-        w[k] = emul::eq2x<POW2>(prev, cur, nxt, m);
+        w[k] = emul::eq2x<POW2, NEG>(prev, cur, nxt, m);
         prev = cur;
         cur = nxt;
       }

@@ -95,7 +95,8 @@ static void check_tile(Tally &t, std::vector<double> u, double r, int T) {
     for (size_t i = 0; i < n; ++i) {
       const size_t l = (i + n - 1) % n, rr = (i + 1) % n;
       w[i] = u[i] + r * ((u[l] - 2.0 * u[i]) + u[rr]);
-      y[i] = m.pow2 ? eq2x<true>(x[l], x[i], x[rr], m) : eq2x<false>(x[l], x[i], x[rr], m);
+      y[i] = m.pow2 ? (m.neg ? eq2x<true, true>(x[l], x[i], x[rr], m) : eq2x<true, false>(x[l], x[i], x[rr], m))
+                    : (m.neg ? eq2x<false, true>(x[l], x[i], x[rr], m) : eq2x<false, false>(x[l], x[i], x[rr], m));
     }
     u.swap(w);
     x.swap(y);
