@@ -190,7 +190,10 @@ int heat_set_segments(heat_ctx *c, int segments);
  * intermediate result normal), else on the FP64 unit.  For r = +-2^k the
  * contiguous layout's FP64-unit tiles that pass the same screen multiply by
  * moving the exponent with an integer add (three FP64-unit operations per
- * point instead of four; the same bits).  HEAT_EINVAL outside -1..32. */
+ * point instead of four; the same bits).  The persistent temporal-blocking
+ * form (HEAT_FORM_PERSIST_TB) takes the same setting; there -1 splits each
+ * work unit's tiles between the two engines the same way at every ring size.
+ * HEAT_EINVAL outside -1..32. */
 int heat_set_emulation(heat_ctx *c, int share);
 
 /* The share of 32 tiles the temporal-blocking form computes on the integer
