@@ -284,7 +284,7 @@ def cpu_baseline(w: dict, seconds: float = 12.0) -> dict:
         total += time.perf_counter() - t0
         steps += chunk
     return {"value": n * steps / total / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle", "host": host_cpu(),
-            "sample": f"first {n} points of the initial state as a ring of their own x {steps} steps "
+            "sample": f"a ring of {n} points with the workload's initial-state recipe x {steps} steps "
                       f"({'binary32 compensated' if w['dtype'] == 'f32c' else 'binary64'}), {total:.1f} s on 1 host core"}
 
 
@@ -309,20 +309,105 @@ def cpu_threaded(w: dict, seconds: float = 8.0) -> dict | None:
         steps += chunk
     return {"value": n * steps / total / 1e9, "unit": UNIT, "cores": cores, "host": host_cpu(),
             "kind": "threaded SPSC-queue stepper (Section 2): one thread per segment",
-            "sample": f"first {n} points of the initial state as a ring of their own, {cores} segments x "
+            "sample": f"a ring of {n} points with the workload's initial-state recipe, {cores} segments x "
                       f"{steps} steps (binary64), {total:.1f} s on {cores} host cores"}
 
 
+def _oracle_units(w: dict):
+    """Endless stream of small pieces of the workload for the CPU oracle, each a
+    call returning the point-steps it advanced, and a description of the sample:
+    single rings take 4 steps at a time on a ring of min(N, 2^22) points built
+    with the workload's initial-state recipe; batches and request streams visit
+    their rings in table or arrival order, up to 32 steps each, then start over."""
+    import oracle
+    from paper_2307_01117_gb300 import workloads
+    if w["kind"] in ("ring", "precision"):
+        n = min(w["nx"] * w["np"], 1 << 22)
+        w2 = dict(w)
+        w2["nx"], w2["np"] = n, 1
+        state = {"u": initial_state(w2)}
+        r = oracle.coef(w["k"], w["dt"], w["dx"])
+        f32 = w["dtype"] == "f32c"
+
+        def unit():
+            u = state["u"]
+            state["u"] = oracle.run_f32c(u, np.float32(r), 4, 1) if f32 else oracle.run(u, r, 4)
+            return 4 * n
+        desc = (f"a ring of {n} points with the workload's initial-state recipe, 4 steps at a time "
+                f"({'binary32 compensated' if f32 else 'binary64'})")
+        while True:
+            yield unit, desc
+    if w["kind"] == "batch":
+        specs = workloads.ring_table(w["count"], seed=w["seed"], nt_lo=w.get("nt_lo", 100), nt_hi=w.get("nt_hi", 5000))
+        rings = [(s.n, s.nt, s.r, s.seed, False, lambda s=s: workloads.ring_initial(s)) for s in specs]
+        desc = "the rings of the batch table in order, up to 32 of each ring's steps (binary64)"
+    else:
+        reqs = workloads.request_stream(w["rate"], w["duration"], seed=w["seed"])
+        rings = [(q.n, q.nt, q.r, q.seed, q.f32c, lambda q=q: workloads.uniform(q.n, q.seed, -1.0, 1.0)) for q in reqs]
+        desc = ("the requests of the arrival stream in order, up to 32 of each request's steps "
+                "(binary64 or binary32 compensated as requested; u0 = U[-1,1) drawn on the host)")
+    while True:
+        for n, nt, r, _, f32, init in rings:
+            steps = min(nt, 32)
+
+            def unit(n=n, r=r, f32=f32, init=init, steps=steps):
+                u = init()
+                if f32:
+                    oracle.run_f32c(u, np.float32(r), steps, 1)
+                else:
+                    oracle.run(u, r, steps)
+                return n * steps
+            yield unit, desc
+
+
+def _oracle_samples(w: dict, count: int, seconds: float, units=None):
+    """`count` samples of at least `seconds` each: (point-steps, seconds) per sample."""
+    units = units or _oracle_units(w)
+    out, desc = [], ""
+    for _ in range(count):
+        done, t0 = 0, time.perf_counter()
+        while True:
+            unit, desc = next(units)
+            done += unit()
+            if time.perf_counter() - t0 >= seconds:
+                break
+        out.append((done, time.perf_counter() - t0))
+    return out, desc, units
+
+
+def reference_config(args, w: dict) -> dict:
+    """The workload as the GPU arm's `config` names it, without device state."""
+    if w["kind"] in ("ring", "precision"):
+        n = w["nx"] * w["np"]
+        return {"workload": args.workload, "nx": w["nx"], "np": w["np"], "N": n, "nt": w["nt"], "k": w["k"],
+                "dt": w["dt"], "dx": w["dx"], "init": w["init"], "arith": args.arith}
+    if w["kind"] == "batch":
+        return {"workload": args.workload, "rings": w["count"], "seed": w["seed"],
+                "nt_range": [w.get("nt_lo", 100), w.get("nt_hi", 5000)]}
+    return {"workload": args.workload, "rate_req_s": w["rate"], "window_s": w["duration"], "seed": w["seed"]}
+
+
 def run_reference(args, w: dict, rank: int) -> None:
+    """--impl reference: the CPU oracle as it stands, single-threaded on the host,
+    on bounded samples of the workload: W warm-up samples of about 0.2 s, then K
+    timed samples of about 2 s (one per bench step).  Under torchrun only rank 0
+    runs it."""
     if rank != 0:
         return
-    cb = cpu_baseline(w, seconds=max(2.0, 2.0 * args.steps))
-    line = {"impl": "reference", "metric": METRIC[w["dtype"]], "value": cb["value"], "unit": UNIT,
-            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": None,
+    _, _, units = _oracle_samples(w, args.warmup, 0.2)
+    samples, desc, _ = _oracle_samples(w, args.steps, 2.0, units)
+    pts = sum(p for p, _ in samples)
+    secs = sum(t for _, t in samples)
+    value = pts / secs / 1e9
+    cb = {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "host": host_cpu(),
+          "sample": f"{desc}; {args.warmup} warm-up samples, then {args.steps} timed samples of about 2 s "
+                    f"({pts:.3g} point-steps in {secs:.1f} s on 1 host core)"}
+    line = {"impl": "reference", "metric": METRIC[w["dtype"]], "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64" if w["dtype"] == "f64" else "f32", "data": "synthetic",
-            "config": {"workload": args.workload}, "cpu_baseline": cb,
-            "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+            "config": reference_config(args, w), "cpu_baseline": cb,
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
