@@ -72,3 +72,18 @@ def test_null_context_is_einval(lib):
     assert lib.heat_sync(None) == H.HEAT_EINVAL
     assert lib.heat_set_form(None, 0, 0) == H.HEAT_EINVAL
     lib.heat_destroy(None)  # no-op
+
+
+def test_plain_c_client_compiles_links_and_runs(lib, tmp_path):
+    """The header is plain C99 and the library links from C (tests/abi_c_client.c)."""
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("needs gcc")
+    libdir = os.path.dirname(H.lib()._name)
+    exe = tmp_path / "abi_c_client"
+    subprocess.check_call(["gcc", "-std=c99", "-Wall", "-Wextra", "-Werror", "-pedantic",
+                           "-I", os.path.join(ROOT, "include"), os.path.join(ROOT, "tests", "abi_c_client.c"),
+                           "-L", libdir, "-lheat", f"-Wl,-rpath,{libdir}", "-lm", "-o", str(exe)])
+    p = subprocess.run([str(exe)], capture_output=True, text=True, timeout=60)
+    assert p.returncode == 0 and "c client ok" in p.stdout, p.stdout + p.stderr
