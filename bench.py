@@ -2,7 +2,8 @@
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
                     [--form auto|plain|persist|tblock|cluster|persist_tb] [--T depth] [--arith exact|fma]
-                    [--layout 0|1] [--split L] [--emul S] [--impl ours|reference]
+                    [--layout 0|1] [--split L] [--emul S] [--k K] [--impl ours|reference]
+                    [--no-e2e] [--no-cpu-baseline] [--rate R] [--duration S] [--tick STEPS]
 
 Workloads (all synthetic, seeded; the paper's own workload is synthetic too):
   ring-2^28-f64   (default) one ring, np = 256 x nx = 2^20, nt = 1000, r = 0.25,
@@ -15,6 +16,14 @@ Workloads (all synthetic, seeded; the paper's own workload is synthetic too):
                   {1,2,4,8,16}, nt uniform in [100, 5000], r uniform in
                   [0.05, 0.5], u0 = U[-1,1) (seed 1), one persistent launch
   batch-256-f64   the first 256 rings of the same table
+  batch-prof-f64  the same 256 rings with nt uniform in [100, 300] (profiling case)
+  precision-2^28  binary32 compensated vs binary64 on the 2^28-point ring, nt = 10000,
+                  u0 = modes 1, 7, 64; errors against a binary64 run and the closed form
+  serve-100, serve-2000
+                  Poisson request streams (100 or 2000 requests/s), N log-uniform in
+                  [1e4, 1e7], nt uniform in [100, 2000], r uniform in [0.05, 0.5],
+                  binary64 / binary32 compensated 50/50, 120 GB state budget; one
+                  step = one arrival window; p50/p99 latency beside GLUP/s
 
 One bench step is one pass of the whole hot path over one batch of input:
 load the initial state from a device-resident copy, advance every ring its nt
@@ -33,8 +42,9 @@ on the same sample.
 Under torchrun (N > 1) every rank runs its own independent replica on its own
 GPU (replicas only: the ring is not sharded across GPUs): weak scaling, no
 data-path collective; `value` is all ranks' point-steps over the slowest rank's
-time.  ``--impl reference`` times the CPU oracle (single thread) on a bounded
-sample of the workload instead.  Rank 0 prints one JSON line.
+time.  ``--impl reference`` times the CPU oracle (single thread, on the host)
+instead: W short warm-up samples, then K timed bounded samples of the workload
+(about 2 s each); only rank 0 runs it.  Rank 0 prints one JSON line.
 """
 from __future__ import annotations
 
