@@ -425,7 +425,9 @@ def run_reference(args, w: dict, rank: int) -> None:
 # Runners, one per workload kind: step(events), e2e_prepare/e2e_run, kernel_info, config.
 
 class RingRunner:
+    """One ring: a step loads u0 from a device copy, runs nt steps and takes the sum."""
     E2E_COPIES = "beside the steps: two contexts on two streams take the steps in turn"
+
     def __init__(self, args, w, H, torch, local, stream):
         self.args, self.w, self.H, self.torch, self.stream = args, w, H, torch, stream
         self.n = w["nx"] * w["np"]
@@ -547,7 +549,10 @@ class RingRunner:
 
 
 class BatchRunner:
+    """Many rings in one batch: a step restores their initial states and runs one
+    batch launch that advances every ring its nt steps."""
     E2E_COPIES = "in series with the steps"
+
     def __init__(self, args, w, H, torch, local, stream):
         from paper_2307_01117_gb300 import workloads
         self.args, self.w, self.H, self.torch, self.stream = args, w, H, torch, stream
@@ -677,10 +682,10 @@ class PrecisionRunner(RingRunner):
 
 
 class ServeRunner:
-    E2E_COPIES = None
     """One step = one window of Poisson arrivals replayed in real time through the
     continuous-batching server (not drained at the window's end: unfinished
     requests count as backlog)."""
+    E2E_COPIES = None
 
     def __init__(self, args, w, H, torch, local, stream):
         from paper_2307_01117_gb300 import serve, workloads
