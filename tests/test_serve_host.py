@@ -1,0 +1,153 @@
+"""Host logic of the continuous-batching server (paper_2307_01117_gb300/serve.py)
+on the CPU: admission by arena space with a bounded lookahead, requests that
+wait for space keep their place, late arrivals join the next tick, oversized
+requests are rejected.  The heat_batch_* calls are replaced by a fake that keeps
+step counts and arena occupancy only (no device, no stencil arithmetic)."""
+import contextlib
+import time
+import types
+
+import numpy as np
+import pytest
+
+from paper_2307_01117_gb300 import serve
+from paper_2307_01117_gb300.workloads import Request
+
+
+class FakeError(RuntimeError):
+    def __init__(self, code):
+        super().__init__(code)
+        self.code = code
+
+
+ENOMEM = -2
+
+
+class FakeBatches:
+    """Arena occupancy in 64-point units; each run advances every ring by up to
+    max_steps and sleeps `tick_s` (a stand-in for the launch)."""
+
+    def __init__(self, caps, tick_s=0.0):
+        self.caps, self.tick_s = caps, tick_s
+        self.rings = {b: {} for b in caps}
+        self.next_id = {b: 0 for b in caps}
+        self.last = {b: 0 for b in caps}
+        self.runs = 0
+
+    def _len(self, n):
+        return -(-(n + 64) // 64) * 64
+
+    def heat_batch_add_device(self, b, nx, np_, k, dt, dx, nt, u):
+        n = nx * np_
+        assert len(u) == n
+        if sum(r["len"] for r in self.rings[b].values()) + self._len(n) > self.caps[b]:
+            raise FakeError(ENOMEM)
+        rid = self.next_id[b]
+        self.next_id[b] += 1
+        self.rings[b][rid] = {"n": n, "len": self._len(n), "left": nt, "done": 0}
+        return rid
+
+    def heat_batch_run(self, b, max_steps):
+        ps = 0
+        for r in self.rings[b].values():
+            s = min(r["left"], max_steps)
+            r["left"] -= s
+            r["done"] += s
+            ps += s * r["n"]
+        self.last[b] = ps
+        self.runs += 1
+        if self.tick_s:
+            time.sleep(self.tick_s)
+
+    def heat_batch_info(self, b):
+        return {"last_point_steps": self.last[b]}
+
+    def heat_batch_sync(self, b):
+        pass
+
+    def heat_batch_query(self, b, rid):
+        r = self.rings[b][rid]
+        return r["done"], r["left"]
+
+    def heat_batch_get(self, b, rid, n):
+        return np.zeros(n)
+
+    def heat_batch_remove(self, b, rid):
+        del self.rings[b][rid]
+
+
+def make_server(monkeypatch, cap_points, tick_steps=16, lookahead=64, tick_s=0.0):
+    fake = FakeBatches({"b64": cap_points, "b32": cap_points}, tick_s)
+    ns = types.SimpleNamespace(HeatError=FakeError, HEAT_ENOMEM=ENOMEM,
+                               **{k: getattr(fake, k) for k in dir(fake) if k.startswith("heat_batch_")})
+    monkeypatch.setattr(serve, "H", ns)
+    srv = object.__new__(serve.HeatServer)
+    srv.torch = types.SimpleNamespace(cuda=types.SimpleNamespace(stream=lambda s: contextlib.nullcontext()))
+    srv.tick_steps, srv.lookahead = tick_steps, lookahead
+    srv.caps = {False: cap_points, True: cap_points}
+    srv.batch = {False: "b64", True: "b32"}
+    srv.stream = srv.stream32 = None
+    srv.init_fn = lambda req: np.zeros(req.n)
+    srv.queue, srv.inflight, srv.keep_alive, srv.results = serve.collections.deque(), {}, [], {}
+    return srv, fake
+
+
+def req(t, n, nt, f32c=False):
+    return Request(t_arrive=t, n=n, nt=nt, r=0.25, f32c=f32c, seed=0)
+
+
+def test_requests_wait_for_space_and_all_complete(monkeypatch):
+    srv, fake = make_server(monkeypatch, cap_points=10_000)
+    reqs = [req(0.0, 4000, 48) for _ in range(5)]        # two fit at a time (2 x 4096 points)
+    st = srv.serve(reqs, drain=True)
+    assert len(st.done) == 5 and st.max_inflight == 2 and not srv.queue and not srv.inflight
+    order = [d.index for d in sorted(st.done, key=lambda d: d.t_done)]
+    assert order[:2] == [0, 1] and sorted(order) == [0, 1, 2, 3, 4]   # waiting requests kept their places
+    assert st.ticks == 3 * 3                                          # 48 steps = 3 ticks of 16, three waves
+    assert all(r == {} for r in fake.rings.values())                  # every arena slot released
+
+
+def test_lookahead_admits_a_small_request_behind_one_that_does_not_fit(monkeypatch):
+    srv, fake = make_server(monkeypatch, cap_points=10_000)
+    st = serve.ServeStats()
+    for i, r in enumerate([req(0.0, 6000, 32), req(0.0, 6000, 32), req(0.0, 1000, 32)]):
+        srv.submit(i, r, st)
+    srv._admit(0.0)
+    admitted = sorted(idx for idx, _, _ in srv.inflight.values())
+    assert admitted == [0, 2] and [i for i, _ in srv.queue] == [1]
+
+
+def test_lookahead_is_bounded(monkeypatch):
+    srv, fake = make_server(monkeypatch, cap_points=10_000, lookahead=2)
+    st = serve.ServeStats()
+    for i, r in enumerate([req(0.0, 9000, 32), req(0.0, 9000, 32), req(0.0, 100, 32)]):
+        srv.submit(i, r, st)
+    srv._admit(0.0)
+    # the first fills the arena, the second does not fit, the third is beyond the lookahead
+    assert sorted(idx for idx, _, _ in srv.inflight.values()) == [0]
+    assert [i for i, _ in srv.queue] == [1, 2]
+
+
+def test_oversized_requests_are_rejected(monkeypatch):
+    srv, fake = make_server(monkeypatch, cap_points=10_000)
+    st = srv.serve([req(0.0, 10_000, 16), req(0.0, 100, 16)], drain=True)
+    assert st.rejected_too_large == 1 and [d.index for d in st.done] == [1]
+    assert st.summary()["backlog"] == 0
+
+
+def test_late_arrival_joins_the_next_tick_beside_a_running_request(monkeypatch):
+    srv, fake = make_server(monkeypatch, cap_points=100_000, tick_s=0.002)
+    reqs = [req(0.0, 2000, 16 * 60), req(0.03, 2000, 16)]   # the first runs about 60 ticks (0.12 s)
+    st = srv.serve(reqs, drain=True)
+    done = {d.index: d for d in st.done}
+    assert st.max_inflight == 2
+    assert done[1].t_admit < done[0].t_done                   # admitted while the first still ran
+    assert done[1].t_done < done[0].t_done                     # and finished first
+    assert st.gpu_point_steps == 2000 * 16 * 60 + 2000 * 16
+
+
+def test_binary32_requests_use_their_own_arena(monkeypatch):
+    srv, fake = make_server(monkeypatch, cap_points=5_000)
+    st = srv.serve([req(0.0, 4000, 16), req(0.0, 4000, 16, f32c=True)], drain=True)
+    assert st.max_inflight == 2 and len(st.done) == 2
+    assert {d.f32c for d in st.done} == {False, True}
