@@ -9,12 +9,15 @@ of checks that pin the oracle (exact rational evolution, rounding of each
 operation, Fourier-mode decay, conservation, the coefficient's reading, the
 compensated form's error bound, light cone and segmented algorithm against the
 plain ring).  The unmodified source passes every check; every mutant fails at
-least one."""
+least one.  Two more mutants of the threaded CPU baseline (oracle/heat_threaded.c:
+edge values sent the wrong way, ghosts taken from the wrong side) must differ
+from the plain ring; they run in a child process with a time limit."""
 import ctypes
 import math
 import os
 import shutil
 import subprocess
+import sys
 from fractions import Fraction
 
 import numpy as np
@@ -211,3 +214,56 @@ def test_planted_mistake_is_caught(name, old, new, tmp_path):
     L = compile_copy(text.replace(old, new), tmp_path, "mutant")
     caught = [c.__name__ for c in CHECKS if not c(L)]
     assert caught, f"no check catches: {name}"
+
+
+# --- the threaded CPU baseline (oracle/heat_threaded.c) -----------------------------------
+
+THREADED_SRC = os.path.join(ROOT, "oracle", "heat_threaded.c")
+
+# (name, text in heat_threaded.c, planted replacement); each mutant still pushes
+# and pops one value per queue and step, so none of them can block
+THREADED_MUTANTS = [
+    ("edge values sent the wrong way", "q_push(g->to_left, c[1]);\n    q_push(g->to_right, c[nx]);",
+     "q_push(g->to_left, c[nx]);\n    q_push(g->to_right, c[1]);"),
+    ("ghosts taken from the wrong side", "c[0] = q_pop(g->from_left);\n    c[nx + 1] = q_pop(g->from_right);",
+     "c[0] = q_pop(g->from_right);\n    c[nx + 1] = q_pop(g->from_left);"),
+]
+
+_THREADED_PROBE = r"""
+import ctypes, sys
+import numpy as np
+lib = ctypes.CDLL(sys.argv[1])
+d, i64, i32, ip, vp = ctypes.c_double, ctypes.c_int64, ctypes.c_int32, ctypes.c_int, ctypes.c_void_p
+lib.heat_threaded_run.restype = ip
+lib.heat_threaded_run.argtypes = [vp, i64, i32, d, i64]
+lib.heat_oracle_run.restype = ip
+lib.heat_oracle_run.argtypes = [vp, vp, i64, d, i64, ip]
+rng = np.random.Generator(np.random.PCG64(3))
+u0 = rng.uniform(-1, 1, 5 * 7)
+a = u0.copy(); w = np.empty_like(a)
+assert lib.heat_oracle_run(a.ctypes.data, w.ctypes.data, a.size, 0.3, 20, 0) == 0
+b = u0.copy()
+assert lib.heat_threaded_run(b.ctypes.data, 7, 5, 0.3, 20) == 0
+print("equal" if np.array_equal(a, b) else "differ")
+"""
+
+
+def threaded_equals_plain(threaded_text, tmp_path, name):
+    src = tmp_path / f"{name}_threaded.c"
+    src.write_text(threaded_text)
+    so = tmp_path / f"{name}.so"
+    subprocess.check_call(["gcc", *oracle.CFLAGS, "-o", str(so), SRC, str(src), "-lm"])
+    p = subprocess.run([sys.executable, "-c", _THREADED_PROBE, str(so)], capture_output=True, text=True, timeout=60)
+    assert p.returncode == 0, p.stderr
+    return p.stdout.strip() == "equal"
+
+
+def test_unmodified_threaded_baseline_equals_the_plain_ring(tmp_path):
+    assert threaded_equals_plain(open(THREADED_SRC).read(), tmp_path, "original")
+
+
+@pytest.mark.parametrize("name,old,new", THREADED_MUTANTS, ids=[m[0] for m in THREADED_MUTANTS])
+def test_planted_mistake_in_the_threaded_baseline_is_caught(name, old, new, tmp_path):
+    text = open(THREADED_SRC).read()
+    assert text.count(old) == 1, name
+    assert not threaded_equals_plain(text.replace(old, new), tmp_path, "mutant")
