@@ -319,7 +319,10 @@ int heat_batch_get(heat_batch *b, int32_t ring_id, double *host_u, int64_t n);
  * error seen at an earlier sync. */
 int heat_batch_get_device(heat_batch *b, int32_t ring_id, double *dev_u, int64_t n);
 
-/* Release a ring's arena space (its id becomes invalid). */
+/* Release a ring's arena space (its id becomes invalid).  Does not wait: work
+ * queued on the batch's stream before the call (a run, a heat_batch_get_device
+ * copy of the ring) still reads the old space, and every later use of that space
+ * is queued behind it on the same stream. */
 int heat_batch_remove(heat_batch *b, int32_t ring_id);
 
 /* Temporal block depth T (1..64) and target segment length in points (>= 512);
@@ -391,15 +394,21 @@ int heat_batch_info(const heat_batch *b, int32_t *live_rings, int64_t *largest_f
  *   n       1 .. 1048576 points (larger rings -> HEAT_EINVAL: the library's one
  *           fixed scratch array holds 2^20 values);
  *   k, dt, dx, arith   as for heat_create / heat_set_arith;
- *   cuda_stream        cudaStream_t the steps are queued on (NULL = default).
+ *   cuda_stream        cudaStream_t the steps are queued on (NULL = default);
+ *                      it must belong to the current device (a stream of
+ *                      another device -> HEAT_EINVAL).
  * Queues nt launches and returns without waiting.  It calls no cudaMalloc,
  * cudaFree or other allocating routine: the buffer a multi-step run needs
  * besides input and output is a fixed 8 MiB device array that every GPU loading
  * this library holds until the process exits.  The first call on each device
  * looks up that array's device address (cudaGetSymbolAddress) with the device
- * current; make that first call before any stream capture.  All calls on a
- * device share the array, so calls whose work overlaps on the GPU (two streams,
- * two host threads) race and must be ordered by the caller. */
+ * current and loads the kernels of both arithmetic readings; make that first
+ * call, in either reading, before any stream capture.  All calls on a device
+ * share the array, so calls whose work overlaps on the GPU (two streams, two
+ * host threads) race and must be ordered by the caller.
+ * HEAT_ECUDA: a CUDA error was already pending on the calling thread (reported,
+ * not cleared; nothing queued), or a launch failed part-way, in which case the
+ * steps queued before it still run and dev_u is undefined. */
 int heat_run_noalloc(const double *dev_u0, double *dev_u, int64_t n, double k, double dt, double dx,
                      int64_t nt, int arith, void *cuda_stream);
 

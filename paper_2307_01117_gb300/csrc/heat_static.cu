@@ -67,9 +67,10 @@ __global__ void __launch_bounds__(kThreads) k_plain_f64_noalloc(const double *__
 }
 
 // Per-device set-up: the scratch array's device address and the SM count.
-int device_setup(double **scratch, int *sms) {
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) return HEAT_ECUDA;
+// Both kernel instantiations are loaded here too (cudaFuncGetAttributes loads
+// a lazily loaded kernel), so that no later call, in either arithmetic, makes
+// the driver load code or allocate memory for it.
+int device_setup(int dev, double **scratch, int *sms) {
   if (dev < 0 || dev >= kMaxDevices) return HEAT_ENOTSUP;
   std::lock_guard<std::mutex> lock(g_setup_mu);
   if (!g_scratch_addr[dev]) {
@@ -77,12 +78,25 @@ int device_setup(double **scratch, int *sms) {
     if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return HEAT_ECUDA;
     int n = 0;
     if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) return HEAT_ECUDA;
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, k_plain_f64_noalloc<false>) != cudaSuccess ||
+        cudaFuncGetAttributes(&fa, k_plain_f64_noalloc<true>) != cudaSuccess)
+      return HEAT_ECUDA;
     g_sms[dev] = n;
     g_scratch_addr[dev] = (double *)p;
   }
   *scratch = g_scratch_addr[dev];
   *sms = g_sms[dev];
   return HEAT_OK;
+}
+
+// The stream must belong to the current device: the scratch address and the
+// launches are the current device's.  NULL and the two special handles
+// (legacy and per-thread default streams) always do.
+bool stream_on_device(cudaStream_t st, int dev) {
+  if (st == nullptr || st == cudaStreamLegacy || st == cudaStreamPerThread) return true;
+  int sdev = -1;
+  return cudaStreamGetDevice(st, &sdev) == cudaSuccess && sdev == dev;
 }
 
 bool overlaps(const double *a, const double *b, int64_t n) {
@@ -104,11 +118,17 @@ extern "C" int heat_run_noalloc(const double *dev_u0, double *dev_u, int64_t n, 
   if (overlaps(dev_u0, dev_u, n)) return HEAT_EINVAL;
   const double r = (k * dt) / (dx * dx);
   if (!isfinite(r)) return HEAT_EINVAL;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return HEAT_ECUDA;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  if (!stream_on_device(st, dev)) return HEAT_EINVAL;
   double *scratch = nullptr;
   int sms = 0;
-  int rc = device_setup(&scratch, &sms);
+  int rc = device_setup(dev, &scratch, &sms);
   if (rc != HEAT_OK) return rc;
-  cudaStream_t st = (cudaStream_t)cuda_stream;
+  // an error left pending by earlier work on this thread is reported, not
+  // cleared, and nothing is queued
+  if (cudaPeekAtLastError() != cudaSuccess) return HEAT_ECUDA;
   if (nt == 0)
     return cudaMemcpyAsync(dev_u, dev_u0, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, st) == cudaSuccess
                ? HEAT_OK

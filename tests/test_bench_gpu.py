@@ -33,3 +33,8 @@ def test_bench_json_line_contract():
     # copies run beside the other context's steps, never instead of them
     assert e["value"] <= 1.1 * d["value"] and e["contexts_agree_bitwise"] is True
     assert d["gpu_launches"] > 0
+    # the plain one-step-per-launch kernel on the same ring, beside the headline
+    pl = d["plain"]
+    assert pl["form"] == "plain" and pl["value"] > 0 and pl["launches_per_step"] == 20
+    assert 0 < pl["hbm"]["frac"] < 1.2 and 0 < pl["fp64_unit"]["frac"] < 1.2
+    assert abs(pl["headline_over_plain"] - d["value"] / pl["value"]) < 1e-9

@@ -21,6 +21,7 @@ import numpy as np
 import pytest
 
 import oracle
+from exact_binary32 import compensated_exact, rn32
 from paper_2307_01117_gb300 import workloads
 
 GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
@@ -55,26 +56,6 @@ def rn(x: Fraction) -> float:
     """Round an exact rational to the nearest binary64, ties to even
     (CPython's int/int true division is correctly rounded)."""
     return x.numerator / x.denominator
-
-
-def rn32(x: Fraction) -> np.float32:
-    """Round an exact rational to the nearest binary32, ties to even (normal range)."""
-    if x == 0:
-        return np.float32(0.0)
-    s = -1 if x < 0 else 1
-    a = abs(x)
-    e = math.floor(math.log2(a.numerator) - math.log2(a.denominator))
-    while Fraction(2) ** e > a:
-        e -= 1
-    while Fraction(2) ** (e + 1) <= a:
-        e += 1
-    q = Fraction(2) ** (e - 23)          # ulp for a 24-bit significand
-    m = a / q
-    fl = math.floor(m)
-    rem = m - fl
-    if rem > Fraction(1, 2) or (rem == Fraction(1, 2) and fl % 2 == 1):
-        fl += 1
-    return np.float32(s * float(fl * q))
 
 
 # --- 1. exact rational brute force --------------------------------------------------
@@ -240,6 +221,29 @@ def test_coefficient_h_squared_reading():
     assert oracle.coef(0.25, 1.0, 1.0) == 0.25
 
 
+# (k, dt, dx) triples of the GPU coefficient tests whose r depends on the
+# evaluation order in its last bits
+ORDER_SENSITIVE = [(0.3286206332490522, 0.030200396783920985, 0.3),
+                   (0.44845565991743563, 0.6130994749175215, 1.3)]
+
+
+@pytest.mark.parametrize("k,dt,dx", ORDER_SENSITIVE)
+def test_coefficient_rounding_of_the_stated_order(k, dt, dx):
+    """r = (k*dt)/(dx*dx): the exact quotient of the two rounded products,
+    rounded once.  Checked with exact fractions; the other evaluation orders
+    (and the 2h and h readings) give other bits for these inputs, so the GPU
+    coefficient tests at these triples tell the readings apart."""
+    K, D, X = Fraction(k), Fraction(dt), Fraction(dx)
+    want = rn(Fraction(rn(K * D)) / Fraction(rn(X * X)))
+    assert oracle.coef(k, dt, dx) == want
+    others = [rn(K * Fraction(rn(D / Fraction(rn(X * X))))),            # k*(dt/(dx*dx))
+              rn(Fraction(rn(Fraction(rn(K * D)) / X)) / X),           # (k*dt/dx)/dx
+              rn(Fraction(rn(K / Fraction(rn(X * X)))) * D),           # (k/(dx*dx))*dt
+              rn(Fraction(rn(K * D)) / Fraction(rn(2 * X))),           # the printed 2h
+              rn(Fraction(rn(K * D)) / X)]                             # a first power of h
+    assert all(o != want for o in others)
+
+
 # --- 7. worked examples (tests/golden) ---------------------------------------------------------
 
 def _golden(name):
@@ -327,6 +331,24 @@ def test_f32c_block_of_one_is_plain_binary32():
         t2 = F(rn32(t1 + ur))
         t3 = F(rn32(F(rf) * t2))
         assert got[i] == rn32(uc + t3), i
+
+
+@pytest.mark.parametrize("T", [2, 3, 5])
+def test_f32c_blocks_longer_than_one_by_value(T):
+    """T > 1 on non-dyadic binary32 data: the carried low part, the TwoSum
+    error term and the end-of-block rounding are each checked by value against
+    the compensated form written out with every binary32 operation rounded
+    once (exact fractions), including a shorter last block."""
+    rng = np.random.Generator(np.random.PCG64(20 + T))
+    n = 11
+    u = rng.uniform(-2, 2, n).astype(np.float32)
+    rf = np.float32(0.3)
+    nt = 2 * T + 1
+    want = compensated_exact(u, rf, nt, T)
+    got = oracle.run_f32c(u, rf, nt, T)
+    assert [float(x) for x in got] == [float(x) for x in want]
+    # the low part matters here: plain binary32 steps (T = 1) give other bits
+    assert [float(x) for x in oracle.run_f32c(u, rf, nt, 1)] != [float(x) for x in want]
 
 
 def test_f32c_error_bound_and_benefit():

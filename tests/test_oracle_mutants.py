@@ -24,6 +24,7 @@ import numpy as np
 import pytest
 
 import oracle
+from exact_binary32 import compensated_exact
 from paper_2307_01117_gb300 import workloads
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -157,6 +158,18 @@ def compensated_block_of_one(L):
     return [Fraction(float(x)) for x in L.f32c(u0, np.float32(0.25), 3, 1)] == q
 
 
+def compensated_by_value(L):
+    # blocks of 2 and 3 steps on non-dyadic binary32 data against the
+    # compensated form with every binary32 operation rounded once
+    rng = np.random.Generator(np.random.PCG64(21))
+    u = rng.uniform(-2, 2, 9).astype(np.float32)
+    for T in (2, 3):
+        want = [float(x) for x in compensated_exact(u, np.float32(0.3), 2 * T + 1, T)]
+        if [float(x) for x in L.f32c(u, np.float32(0.3), 2 * T + 1, T)] != want:
+            return False
+    return True
+
+
 def light_cone(L):
     u0 = workloads.uniform(300, 8, -1, 1)
     idx = [0, 1, 17, 150, 298, 299]
@@ -169,7 +182,8 @@ def segmented(L):
 
 
 CHECKS = [exact_rationals, rounding_order, fourier_decay, conservation, coefficient_reading,
-          fused_reading_close, compensated_bound, compensated_block_of_one, light_cone, segmented]
+          fused_reading_close, compensated_bound, compensated_block_of_one, compensated_by_value, light_cone,
+          segmented]
 
 # (name, text in heat_oracle.c, planted replacement)
 MUTANTS = [
@@ -184,6 +198,12 @@ MUTANTS = [
      "v[i] = fma(r, fma(-1.0, u[i], ul) + ur, u[i]);"),
     ("compensation term dropped", "l2[i] = l[i] + err;", "l2[i] = l[i];"),
     ("low parts left out of the difference", "float d = dh + dl;", "float d = dh;"),
+    ("low part not accumulated", "l2[i] = l[i] + err;", "l2[i] = err;"),
+    ("TwoSum error without its second term", "float ee = (a - (ss - bb)) + (b - bb);",
+     "float ee = (a - (ss - bb));"),
+    ("sign of the low parts' 2l flipped", "float dl = (l[im] - 2.0f * l[i]) + l[ip];",
+     "float dl = (l[im] + 2.0f * l[i]) + l[ip];"),
+    ("low part dropped at the block's end", "u[i] = h[i] + l[i];", "u[i] = h[i];"),
     ("light cone read one place off", "out[q] = w[nt];", "out[q] = w[nt + 1 < W ? nt + 1 : nt];"),
     ("ghost queues swapped", "c[0] = fifo_pop(&from_left[p]);\n      c[nx + 1] = fifo_pop(&from_right[p]);",
      "c[0] = fifo_pop(&from_right[p]);\n      c[nx + 1] = fifo_pop(&from_left[p]);"),

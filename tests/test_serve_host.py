@@ -2,7 +2,8 @@
 on the CPU: admission by arena space with a bounded lookahead, requests that
 wait for space keep their place, late arrivals join the next tick, oversized
 requests are rejected.  The heat_batch_* calls are replaced by a fake that keeps
-step counts and arena occupancy only (no device, no stencil arithmetic)."""
+step counts and arena occupancy only (no device, no stencil arithmetic); its
+runs and result copies count as complete as soon as they are queued."""
 import contextlib
 import time
 import types
@@ -55,7 +56,7 @@ class FakeBatches:
             r["done"] += s
             ps += s * r["n"]
         self.last[b] = ps
-        self.runs += 1
+        self.runs += ps > 0            # runs that had work
         if self.tick_s:
             time.sleep(self.tick_s)
 
@@ -88,8 +89,15 @@ def make_server(monkeypatch, cap_points, tick_steps=16, lookahead=64, tick_s=0.0
     srv.batch = {False: "b64", True: "b32"}
     srv.stream = srv.stream32 = None
     srv.init_fn = lambda req: np.zeros(req.n)
-    srv.queue, srv.inflight, srv.keep_alive, srv.results = serve.collections.deque(), {}, [], {}
+    srv.max_queued_runs = 2
+    srv._reset_queues()
+    # the fake's runs and copies are complete when queued
+    srv._mark = lambda f32: READY
+    srv._result_copy = lambda f32, rid, n: (np.zeros(n), READY)
     return srv, fake
+
+
+READY = types.SimpleNamespace(query=lambda: True)
 
 
 def req(t, n, nt, f32c=False):
@@ -151,3 +159,36 @@ def test_binary32_requests_use_their_own_arena(monkeypatch):
     st = srv.serve([req(0.0, 4000, 16), req(0.0, 4000, 16, f32c=True)], drain=True)
     assert st.max_inflight == 2 and len(st.done) == 2
     assert {d.f32c for d in st.done} == {False, True}
+
+
+class Flag:
+    """A stand-in for a CUDA event that the test completes by hand."""
+
+    def __init__(self):
+        self.ready = False
+
+    def query(self):
+        return self.ready
+
+
+def test_runs_queue_ahead_and_results_count_when_their_copy_lands(monkeypatch):
+    srv, fake = make_server(monkeypatch, cap_points=100_000)
+    runs, copies = [], []
+    srv._mark = lambda f32: runs.append(Flag()) or runs[-1]
+    srv._result_copy = lambda f32, rid, n: (np.zeros(n), copies.append(Flag()) or copies[-1])
+    st = serve.ServeStats()
+    srv.submit(0, req(0.0, 1000, 16 * 5), st)
+    srv.submit(1, req(0.0, 1000, 16), st)
+    srv.tick(0.0, st)
+    srv.tick(0.0, st)
+    assert fake.runs == 2 and len(runs) == 2              # two runs queued, none complete yet
+    srv.tick(0.0, st)
+    assert fake.runs == 2                                 # the run queue is full: the host does not wait, it skips
+    assert len(copies) == 1 and not st.done               # request 1 finished in run 1; its copy is in flight
+    assert fake.rings["b64"].keys() == {0}                # and its space was released when the copy was queued
+    runs[0].ready = True
+    srv.tick(0.0, st)
+    assert fake.runs == 3 and not st.done
+    copies[0].ready = True
+    srv.tick(0.0, st)
+    assert [d.index for d in st.done] == [1]
