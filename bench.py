@@ -37,7 +37,11 @@ on two streams take the steps in turn, so one context's copies run while the
 other advances its ring).  `cpu_baseline` is the CPU oracle,
 single-threaded, on a bounded sample; `cpu_threaded` is the paper's parallel
 algorithm (one host thread per segment, SPSC ghost queues) on every host core,
-on the same sample.
+on the same sample.  Binary64 ring lines also carry `plain`: the plain
+one-step-per-launch kernel on the same ring in the same run (GLUP/s, its HBM
+fraction at 16 B per point-step and its FP64-unit fraction); the default line
+also carries `serving`: a 10 s window of 100 requests/s through the
+continuous-batching server (p50/p99 latency, GLUP/s, backlog).
 
 Under torchrun (N > 1) every rank runs its own independent replica on its own
 GPU (replicas only: the ring is not sharded across GPUs): weak scaling, no
@@ -760,6 +764,65 @@ class ServeRunner:
 
 
 # ---------------------------------------------------------------------------------------------
+# Sub-records of the default line: the plain one-step-per-launch kernel on the same
+# ring, and a short serving window
+
+def plain_subrecord(args, w, H, torch, local, stream, sms: int, pk: dict, steps: int = 2) -> dict:
+    """The same ring advanced by the plain form (one launch per step): GLUP/s with
+    its HBM fraction (16 B per point-step, binary64) and its FP64-unit fraction,
+    timed like the headline (CUDA events around heat_run, one warm-up step that
+    also captures the run's CUDA graph)."""
+    r = w["k"] * w["dt"] / (w["dx"] * w["dx"])
+    n, nt = w["nx"] * w["np"], w["nt"]
+    u0 = torch.from_numpy(initial_state(w)).to(f"cuda:{local}")
+    with H.Heat(w["nx"], w["np"], w["k"], w["dt"], w["dx"], dtype=w["dtype"], form="plain", stream=stream) as h:
+        ms = []
+        for i in range(steps + 1):
+            H.heat_set_device(h.ctx, u0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            H.heat_run(h.ctx, nt)
+            e1.record(stream)
+            h.sync()
+            if i:
+                ms.append(e0.elapsed_time(e1))
+        launches = H.heat_last_run(h.ctx)["launches"]
+    del u0
+    glups = n * nt / (statistics.mean(ms) * 1e-3) / 1e9
+    elem = 8.0 if w["dtype"] == "f64" else 4.0
+    dp_ops = 3 if (args.arith == "exact" and is_pow2(r)) else DP_OPS[args.arith]
+    f_peak = 2.0 * sms * pk["sm_max_mhz"] * 1e6 / dp_ops / 1e9
+    hbm_gbs = glups * 2 * elem
+    return {"kernel": "k_plain_f64" if w["dtype"] == "f64" else "k_plain_f32c", "form": "plain",
+            "value": glups, "unit": UNIT, "steps": steps, "launches_per_step": launches,
+            "hbm": {"achieved": hbm_gbs, "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": hbm_gbs / pk["hbm_gbs"],
+                    "bytes_per_point_step": 2 * elem},
+            "fp64_unit": {"achieved": glups, "peak": f_peak, "unit": "GLUP/s", "frac": glups / f_peak,
+                          "fp64_ops_per_point_step": dp_ops} if w["dtype"] == "f64" else None,
+            "headline_over_plain": None}
+
+
+def serving_subrecord(stream, rate: float = 100.0, duration: float = 10.0, tick: int = 256,
+                      budget: float = 120e9) -> dict:
+    """A short serving window (Poisson arrivals replayed in real time through the
+    continuous-batching server, not drained): p50/p99 latency, GLUP/s, backlog."""
+    from paper_2307_01117_gb300 import serve, workloads
+    srv = serve.HeatServer(budget_bytes=budget, tick_steps=tick, stream=stream)
+    try:
+        srv.serve(workloads.request_stream(rate=rate, duration=2.0, seed=1002), duration=2.0)   # warm-up
+        st = srv.serve(workloads.request_stream(rate=rate, duration=duration, seed=2), duration=duration)
+    finally:
+        srv.close()
+    s = st.summary()
+    return {"rate_req_s": rate, "window_s": duration, "tick_steps": tick, "budget_bytes": budget,
+            "p50_s": s["p50_s"], "p99_s": s["p99_s"], "submitted": s["submitted"], "completed": s["completed"],
+            "backlog_at_window_end": s["backlog"], "completed_glups": s["completed_glups"],
+            "advanced_glups": s["advanced_glups"], "max_inflight": s["max_inflight"],
+            "requests": "N log-uniform [1e4, 1e7], nt uniform [100, 2000], r uniform [0.05, 0.5], "
+                        "binary64 / binary32-compensated 50/50 (seed 2)"}
+
+
+# ---------------------------------------------------------------------------------------------
 
 def main() -> int:
     ap = argparse.ArgumentParser()
@@ -781,6 +844,8 @@ def main() -> int:
     ap.add_argument("--rate", type=float, default=0.0, help="serving workloads: arrivals per second")
     ap.add_argument("--duration", type=float, default=0.0, help="serving workloads: window length (s)")
     ap.add_argument("--tick", type=int, default=256, help="serving workloads: steps per tick")
+    ap.add_argument("--no-plain", action="store_true", help="leave out the plain-form sub-record")
+    ap.add_argument("--no-serving", action="store_true", help="leave out the serving sub-record")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     w = dict(WORKLOADS[args.workload])
@@ -908,6 +973,15 @@ def main() -> int:
                "d2h_bytes_per_step": bo, "steps": k_e2e, "copies": runner.E2E_COPIES,
                "contexts_agree_bitwise": runner.e2e_agree()}
 
+    # the default line carries the plain kernel on the same ring and a short
+    # serving window beside the headline (outside its timed region)
+    plain = serving = None
+    if w["kind"] == "ring" and w["dtype"] == "f64" and not args.no_plain and ki["form"] != "plain":
+        plain = plain_subrecord(args, w, H, torch, local, stream, sms, pk)
+        plain["headline_over_plain"] = value / plain["value"]
+    if args.workload == DEFAULT_WORKLOAD and not args.no_serving:
+        serving = serving_subrecord(stream)
+
     cb = ct = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and w["kind"] != "serve":
         cb = cpu_baseline(w)
@@ -926,6 +1000,10 @@ def main() -> int:
             "e2e": e2e,
             "gpu_launches": launches, "clocks": clk,
         }
+        if plain is not None:
+            line["plain"] = plain
+        if serving is not None:
+            line["serving"] = serving
         if w["kind"] == "precision":
             line["accuracy"] = runner.accuracy()
         if w["kind"] == "serve":

@@ -803,8 +803,9 @@ int heat_batch_get_device(heat_batch *b, int32_t ring_id, double *dev_u, int64_t
 
 int heat_batch_remove(heat_batch *b, int32_t ring_id) {
   if (!b || !ring_ok(b, ring_id)) return HEAT_EINVAL;
-  // queued work may still touch the ring's space
-  if (cudaStreamSynchronize(b->stream) != cudaSuccess) return HEAT_ECUDA;
+  // no wait: work queued before this call may still touch the ring's space,
+  // but every later use of that space (an admitted ring's copy, a run, a
+  // restore) is queued on the same stream behind it
   auto &r = b->rings[ring_id];
   arena_free(b, r.off, r.len);
   r.live = false;
@@ -1019,10 +1020,17 @@ int heat_batch_autotune(heat_batch *b, int *T_out, int64_t *seg_out) {
 
 namespace heat {
 
-// HEAT_FORM_PERSIST_TB for a single ring: the work-table kernel over one ring
-// whose two buffers are the context's own, segments sized so that the levels
-// keep every CTA busy.  One launch advances all nt steps.
+// HEAT_FORM_PERSIST_TB for a single ring: one launch advances all nt steps.
+// Rings of at least three warp windows take the warp-granular dependency
+// kernel (k_wave.cu); shorter rings the work-table kernel over one ring whose
+// two buffers are the context's own, segments sized so that the levels keep
+// every CTA busy.
 int run_persist_tb(heat_ctx *c, int64_t nt) {
+  {
+    const int T = c->T > 0 ? c->T : (c->dtype == HEAT_F32C ? 32 : 12);
+    const int rc = run_wave(c, nt, T);
+    if (rc != HEAT_ENOTSUP) return rc;
+  }
   if (!c->ptb) {
     heat_batch *b = new (std::nothrow) heat_batch();
     if (!b) return HEAT_ENOMEM;

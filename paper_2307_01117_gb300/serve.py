@@ -4,16 +4,28 @@ Requests (ring size, steps, coefficient, binary64 or binary32-compensated) are
 admitted into two device arenas (the batched-ring runtime, heat_batch_* in
 include/heat.h) as space frees up: admission is by free device memory under a
 byte budget, and a request's state stays resident on the device from admission
-to completion.  Every tick advances all admitted requests of each arena by up
-to `tick_steps` steps in one persistent launch per arena, so requests that
-arrive while others are running join the next tick and their work overlaps on
-the device.  A finished request's state is copied to host memory and its arena
-space released.
+to completion.  Each run advances all admitted requests of an arena by up to
+`tick_steps` steps in one persistent launch, so requests that arrive while
+others are running join the next run and their work overlaps on the device.
 
-Latency is measured from a request's arrival to the moment its result is on the
-host.  With `tick_steps` a multiple of the binary32 block depth T, each result
-is bitwise the one the request gets alone (binary64: heat_run; binary32: the
-temporal-blocking form with block depth T).
+The loop never waits for the device.  Each arena keeps up to `max_queued_runs`
+runs queued on its stream (one running, the next behind it), so the GPU has
+its next run while the host admits arrivals and collects results.  When a run
+that finishes a request is queued, the request's final state is copied, on the
+same stream, to a device buffer and from there to pinned host memory, an event
+is recorded behind the copy, and the request's arena space is released at
+once (every later use of that space is queued behind the copy on the same
+stream).  The host polls those events; latency runs from a request's arrival
+to the moment the host sees its result in host memory.  Device errors (a
+bounded wait that ran out) surface at the end of serve(), when both arenas are
+synchronised.
+
+The arenas split the budget by the expected byte share of the request mix
+(binary64 points cost 16 bytes in two buffers, binary32 points 8: a 50/50 mix
+by count puts one third of the bytes in binary32).  With `tick_steps` a
+multiple of the binary32 block depth T, each result is bitwise the one the
+request gets alone (binary64: heat_run; binary32: the temporal-blocking form
+with block depth T).
 """
 from __future__ import annotations
 
@@ -73,11 +85,13 @@ class HeatServer:
     """budget_bytes: device memory for ring state (both arenas, both buffers)."""
 
     def __init__(self, budget_bytes: float, tick_steps: int = 256, lookahead: int = 64, f32c_share: float = 1 / 3,
-                 T64: int = 0, T32: int = 16, stream=None, init_fn=None, ctas64: int = 3, ctas32: int = 2):
+                 T64: int = 0, T32: int = 16, stream=None, init_fn=None, ctas64: int = 3, ctas32: int = 2,
+                 max_queued_runs: int = 2):
         import torch
         self.torch = torch
         self.tick_steps = int(tick_steps)
         self.lookahead = int(lookahead)
+        self.max_queued_runs = max(1, int(max_queued_runs))
         # binary64 points cost 16 bytes (two buffers), binary32 points 8 bytes
         cap32 = max(1, int(budget_bytes * f32c_share) // 8)
         cap64 = max(1, int(budget_bytes * (1 - f32c_share)) // 16)
@@ -99,16 +113,46 @@ class HeatServer:
         if self.tick_steps % T32:
             raise ValueError("tick_steps must be a multiple of the binary32 block depth")
         self.init_fn = init_fn or self._device_uniform
+        self._reset_queues()
+
+    def _reset_queues(self) -> None:
         self.queue: collections.deque = collections.deque()
         self.inflight: dict = {}   # (f32c, ring id) -> (index, request, t_admit)
-        self.keep_alive: list = []  # device inputs whose copies are still queued
+        self.runs: dict = {False: collections.deque(), True: collections.deque()}  # events behind queued runs
+        self.pending: list = []    # result copies in flight: (event, host array, index, request, t_admit)
         self.results: dict = {}    # index -> host array (when keep_results)
+
+    # -- device specifics (stream-ordered work and events) ----------------------------------------
+
+    def _arena_stream(self, f32: bool):
+        return self.stream32 if f32 else self.stream
 
     def _device_uniform(self, req: Request):
         torch = self.torch
         g = torch.Generator(device="cuda")
         g.manual_seed(req.seed)
         return torch.empty(req.n, dtype=torch.float64, device="cuda").uniform_(-1.0, 1.0, generator=g)
+
+    def _mark(self, f32: bool):
+        """An event recorded now on the arena's stream."""
+        ev = self.torch.cuda.Event()
+        ev.record(self._arena_stream(f32))
+        return ev
+
+    def _result_copy(self, f32: bool, rid: int, n: int):
+        """Queue a finished ring's state to pinned host memory on the arena's
+        stream (device buffer, then host); returns (host array, event)."""
+        torch = self.torch
+        s = self._arena_stream(f32)
+        with torch.cuda.stream(s):          # the buffer belongs to the stream that uses it
+            dev = torch.empty(n, dtype=torch.float64, device="cuda")
+        H.heat_batch_get_device(self.batch[f32], rid, dev, n)
+        host = torch.empty(n, dtype=torch.float64, pin_memory=True)
+        with torch.cuda.stream(s):
+            host.copy_(dev, non_blocking=True)
+        return host.numpy(), self._mark(f32)
+
+    # ---------------------------------------------------------------------------------------------
 
     def close(self):
         for b in self.batch.values():
@@ -129,7 +173,7 @@ class HeatServer:
             index, req = self.queue.popleft()
             looked += 1
             b = self.batch[req.f32c]
-            with self.torch.cuda.stream(self.stream32 if req.f32c else self.stream):  # the copy's stream
+            with self.torch.cuda.stream(self._arena_stream(req.f32c)):  # the copy's stream
                 u = self.init_fn(req)
             try:
                 rid = H.heat_batch_add_device(b, req.n, 1, req.r, 1.0, 1.0, req.nt, u)
@@ -138,39 +182,62 @@ class HeatServer:
                     raise
                 kept.append((index, req))   # no room yet: keep its place
                 continue
-            self.keep_alive.append(u)
             self.inflight[(req.f32c, rid)] = (index, req, now)
         kept.extend(self.queue)
         self.queue = kept
 
-    def tick(self, t0: float, stats: ServeStats, keep_results: bool = False) -> int:
-        """Admit, advance every admitted request by up to tick_steps, collect the
-        finished ones.  Returns the number of requests still in flight."""
-        self._admit(time.perf_counter() - t0)
-        if not self.inflight:
-            return 0
-        stats.max_inflight = max(stats.max_inflight, len(self.inflight))
-        for f32, b in self.batch.items():
-            H.heat_batch_run(b, self.tick_steps)
-            stats.gpu_point_steps += H.heat_batch_info(b)["last_point_steps"]
-        for b in self.batch.values():
-            H.heat_batch_sync(b)
-        self.keep_alive.clear()
+    def _collect(self, t0: float, stats: ServeStats, keep_results: bool) -> None:
+        """Record the requests whose results have reached host memory."""
+        still = []
+        for ev, host, index, req, t_admit in self.pending:
+            if ev.query():
+                stats.done.append(Done(index, req.t_arrive, t_admit, time.perf_counter() - t0, req.n, req.nt,
+                                       req.f32c))
+                if keep_results:
+                    self.results[index] = host
+            else:
+                still.append((ev, host, index, req, t_admit))
+        self.pending = still
+
+    def _launch(self, f32: bool, stats: ServeStats) -> bool:
+        """Queue one run of the arena if it has work and room in its run queue;
+        queue the result copies of the requests the run finishes."""
+        runs = self.runs[f32]
+        while runs and runs[0].query():
+            runs.popleft()
+        if len(runs) >= self.max_queued_runs:
+            return False
+        b = self.batch[f32]
+        H.heat_batch_run(b, self.tick_steps)
+        ps = H.heat_batch_info(b)["last_point_steps"]
+        if ps == 0:
+            return False
+        stats.gpu_point_steps += ps
         stats.ticks += 1
-        finished = []
-        for key, (index, req, t_admit) in self.inflight.items():
-            f32, rid = key
-            if H.heat_batch_query(self.batch[f32], rid)[1] == 0:
-                finished.append(key)
+        finished = [key for key in self.inflight
+                    if key[0] == f32 and H.heat_batch_query(b, key[1])[1] == 0]
         for key in finished:
-            f32, rid = key
             index, req, t_admit = self.inflight.pop(key)
-            out = H.heat_batch_get(self.batch[f32], rid, req.n)
-            H.heat_batch_remove(self.batch[f32], rid)
-            stats.done.append(Done(index, req.t_arrive, t_admit, time.perf_counter() - t0, req.n, req.nt, f32))
-            if keep_results:
-                self.results[index] = out
-        return len(self.inflight)
+            host, ev = self._result_copy(f32, key[1], req.n)
+            # the space is free for rings admitted later: their copies and runs
+            # are queued behind this copy on the same stream
+            H.heat_batch_remove(b, key[1])
+            self.pending.append((ev, host, index, req, t_admit))
+        runs.append(self._mark(f32))
+        return True
+
+    def tick(self, t0: float, stats: ServeStats, keep_results: bool = False) -> int:
+        """Collect finished results, admit arrivals, queue a run on each arena
+        that has room for one.  Returns the number of requests in flight."""
+        self._collect(t0, stats, keep_results)
+        self._admit(time.perf_counter() - t0)
+        stats.max_inflight = max(stats.max_inflight, len(self.inflight))
+        launched = False
+        for f32 in (False, True):
+            launched |= self._launch(f32, stats)
+        if not launched and (self.inflight or self.pending):
+            time.sleep(2e-4)   # the device is busy with queued runs
+        return len(self.inflight) + len(self.pending)
 
     def serve(self, requests: list[Request], duration: float | None = None, drain: bool = False,
               keep_results: bool = False) -> ServeStats:
@@ -178,6 +245,7 @@ class HeatServer:
         Stops at `duration` (default: the last arrival) unless drain is set, in
         which case it runs until every admitted or queued request is done."""
         stats = ServeStats()
+        self._reset_queues()
         reqs = sorted(enumerate(requests), key=lambda x: x[1].t_arrive)
         horizon = duration if duration is not None else (reqs[-1][1].t_arrive if reqs else 0.0)
         t0 = time.perf_counter()
@@ -190,11 +258,13 @@ class HeatServer:
             arrivals_left = nxt < len(reqs) and reqs[nxt][1].t_arrive <= horizon
             if now >= horizon and not drain:
                 break
-            if not self.queue and not self.inflight:
+            if not self.queue and not self.inflight and not self.pending:
                 if not arrivals_left:
                     break
                 time.sleep(max(0.0, min(0.01, reqs[nxt][1].t_arrive - now)))
                 continue
             self.tick(t0, stats, keep_results)
         stats.wall_s = time.perf_counter() - t0
+        for b in self.batch.values():      # report a device error of the window, if any
+            H.heat_batch_sync(b)
         return stats
