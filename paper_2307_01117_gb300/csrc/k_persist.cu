@@ -15,8 +15,8 @@
 // Every wait is bounded by an iteration cap and a %globaltimer deadline; a wait
 // that runs out records HEAT_ETIMEOUT in the device status word, raises the
 // shared abort flag (so the other CTAs stop waiting) and the kernel returns
-// normally.  Within a segment, points are processed as in the plain form (64-
-// point warp tiles, 16-byte vectors, shuffles for in-tile neighbours).
+// normally.  Within a segment, points are processed as in the plain form (groups
+// of four 64-point warp tiles, 16-byte vectors, shuffles for in-tile neighbours).
 #include <string.h>
 
 #include "dp_emul.cuh"
@@ -121,8 +121,15 @@ struct Elem<2> {
 };
 
 // One step over the segment [lo, hi) of src into dst with the given ghosts.
-// src was written earlier in this same launch, so it is read with plain
-// L2-cached loads (never the read-only non-coherent path).
+// src was written earlier in this same launch, so it is read with L2-cached
+// loads (never the read-only non-coherent path).  A warp takes kGroup
+// consecutive 64-point tiles at a time (16-byte vectors, neighbours by shuffle,
+// two edge values per group), so each lane has 2*kGroup independent updates to
+// interleave and a group is screened once for the r = +-2^k multiply; the
+// partial tiles at the segment's ends and the tiles left over after the groups
+// are done point by point.
+constexpr int kGroup = 4;
+
 template <int MODE>
 __device__ __forceinline__ void step_segment(const typename Elem<MODE>::T *src, typename Elem<MODE>::T *dst,
                                              int64_t lo, int64_t hi,
@@ -134,46 +141,61 @@ __device__ __forceinline__ void step_segment(const typename Elem<MODE>::T *src, 
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
   const int nwarps = blockDim.x >> 5;
-  const int64_t t0 = lo >> 6;
-  const int64_t t1 = (hi + 63) >> 6;
-  for (int64_t t = t0 + warp; t < t1; t += nwarps) {
-    const int64_t b = t << 6;
-    if (b >= lo && b + 64 <= hi) {
-      const V x = __ldcg(reinterpret_cast<const V *>(src + b) + lane);
-      T left = __shfl_up_sync(kFull, x.y, 1);
-      T right = __shfl_down_sync(kFull, x.x, 1);
-      if (lane == 0) left = b == lo ? gl : __ldcg(src + b - 1);
-      if (lane == 31) right = b + 64 == hi ? gr : __ldcg(src + b + 64);
+  const int64_t tf = (lo + 63) >> 6;       // first tile inside the segment
+  const int64_t tl = hi >> 6;              // tiles [tf, tl) lie inside
+  const int64_t ngroups = tl > tf ? (tl - tf) / kGroup : 0;
+  for (int64_t q = warp; q < ngroups; q += nwarps) {
+    const int64_t b0 = (tf + q * kGroup) << 6;
+    V x[kGroup];
+#pragma unroll
+    for (int j = 0; j < kGroup; ++j) x[j] = __ldcg(reinterpret_cast<const V *>(src + b0 + 64 * j) + lane);
+    T eleft = T(0), eright = T(0);
+    if (lane == 0) eleft = b0 == lo ? gl : __ldcg(src + b0 - 1);
+    if (lane == 31) eright = b0 + 64 * kGroup == hi ? gr : __ldcg(src + b0 + 64 * kGroup);
+    bool p2 = false;
+    if constexpr (MODE == 0) {
+      if (a.p2) {
+        auto in = [&](double v) { return emul::in_domain((uint64_t)__double_as_longlong(v), a.dom_lo, a.dom_hi); };
+        bool ok = in(eleft) && in(eright);
+#pragma unroll
+        for (int j = 0; j < kGroup; ++j) ok = ok && in(x[j].x) && in(x[j].y);
+        p2 = __all_sync(kFull, ok);
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < kGroup; ++j) {
+      T left = __shfl_up_sync(kFull, x[j].y, 1);
+      T right = __shfl_down_sync(kFull, x[j].x, 1);
+      const T prev_y = __shfl_sync(kFull, x[j > 0 ? j - 1 : 0].y, 31);
+      const T next_x = __shfl_sync(kFull, x[j + 1 < kGroup ? j + 1 : kGroup - 1].x, 0);
+      if (lane == 0) left = j > 0 ? prev_y : eleft;
+      if (lane == 31) right = j + 1 < kGroup ? next_x : eright;
       V y;
-      bool p2 = false;
       if constexpr (MODE == 0) {
-        if (a.p2) {
-          const bool ok = emul::in_domain((uint64_t)__double_as_longlong(left), a.dom_lo, a.dom_hi) &&
-                          emul::in_domain((uint64_t)__double_as_longlong(x.x), a.dom_lo, a.dom_hi) &&
-                          emul::in_domain((uint64_t)__double_as_longlong(x.y), a.dom_lo, a.dom_hi) &&
-                          emul::in_domain((uint64_t)__double_as_longlong(right), a.dom_lo, a.dom_hi);
-          p2 = __all_sync(kFull, ok);
-        }
         if (p2) {
-          y.x = eq2_exact_pow2(left, x.x, x.y, a.p2_hi_add, a.p2_hi_xor);
-          y.y = eq2_exact_pow2(x.x, x.y, right, a.p2_hi_add, a.p2_hi_xor);
+          y.x = eq2_exact_pow2(left, x[j].x, x[j].y, a.p2_hi_add, a.p2_hi_xor);
+          y.y = eq2_exact_pow2(x[j].x, x[j].y, right, a.p2_hi_add, a.p2_hi_xor);
         }
       }
       if (!p2) {
-        y.x = E::upd(left, x.x, x.y, r, rf);
-        y.y = E::upd(x.x, x.y, right, r, rf);
+        y.x = E::upd(left, x[j].x, x[j].y, r, rf);
+        y.y = E::upd(x[j].x, x[j].y, right, r, rf);
       }
-      reinterpret_cast<V *>(dst + b)[lane] = y;
-    } else {
-      for (int j = lane; j < 64; j += 32) {
-        const int64_t g = b + j;
-        if (g < lo || g >= hi) continue;
-        const T ul = g == lo ? gl : __ldcg(src + g - 1);
-        const T ur = g == hi - 1 ? gr : __ldcg(src + g + 1);
-        dst[g] = E::upd(ul, __ldcg(src + g), ur, r, rf);
-      }
+      reinterpret_cast<V *>(dst + b0 + 64 * j)[lane] = y;
     }
   }
+  // the rest point by point: [lo, tf*64), tiles after the groups, [tl*64, hi)
+  const int64_t g0 = tf > tl ? hi : ((tf + ngroups * kGroup) << 6), g1 = tf > tl ? hi : (tl << 6);
+  auto point = [&](int64_t g) {
+    const T ul = g == lo ? gl : __ldcg(src + g - 1);
+    const T ur = g == hi - 1 ? gr : __ldcg(src + g + 1);
+    dst[g] = E::upd(ul, __ldcg(src + g), ur, r, rf);
+  };
+  const int64_t head_end = tf > tl ? hi : (tf << 6);
+  for (int64_t g = lo + threadIdx.x; g < head_end; g += blockDim.x) point(g);
+  for (int64_t g = g0 + threadIdx.x; g < g1; g += blockDim.x) point(g);
+  if (tf <= tl)
+    for (int64_t g = (tl << 6) + threadIdx.x; g < hi; g += blockDim.x) point(g);
 }
 
 template <int MODE>
