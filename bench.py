@@ -327,6 +327,39 @@ def cpu_threaded(w: dict, seconds: float = 8.0) -> dict | None:
                       f"{steps} steps (binary64), {total:.1f} s on {cores} host cores"}
 
 
+def cpu_report() -> dict:
+    """CPU baselines on the paper-shaped configurations, each run in full: the
+    oracle single-threaded on C0 (10^6 points x 1000 steps, u0 = g, r = 1/4; the
+    paper's Fig. 3 workload, Section 6) and on C1 (np = 4 x nx = 1000, 100 steps,
+    r = 1/2), and the threaded SPSC-queue stepper (Section 2) on C0 at the
+    paper's thread counts 2, 20 and 40 (Section 5's T_average) and at the host's
+    core count; counts above the core count oversubscribe the host."""
+    import oracle
+    from paper_2307_01117_gb300 import workloads
+    out = {"host": host_cpu(), "cores": os.cpu_count()}
+
+    def timed(fn):
+        t0 = time.perf_counter()
+        fn()
+        return time.perf_counter() - t0
+
+    u0 = workloads.ramp(10**6)
+    t = timed(lambda: oracle.run(u0, 0.25, 1000))
+    out["C0_oracle"] = {"N": 10**6, "nt": 1000, "threads": 1, "seconds": t, "glups": 1e9 / t / 1e9}
+    u1 = workloads.ramp(4000)
+    t = timed(lambda: oracle.run(u1, 0.5, 100))
+    out["C1_oracle"] = {"N": 4000, "nt": 100, "threads": 1, "seconds": t, "glups": 4e5 / t / 1e9}
+    rows = []
+    for th in sorted({2, 20, 40, os.cpu_count() or 1}):
+        n = 10**6 // th * th      # equal segments
+        u = workloads.ramp(n)
+        t = timed(lambda: oracle.run_threaded(u, th, 0.25, 1000))
+        rows.append({"threads": th, "N": n, "nt": 1000, "seconds": t, "glups": n * 1000 / t / 1e9,
+                     "oversubscribed": th > (os.cpu_count() or 1)})
+    out["C0_threaded"] = rows
+    return out
+
+
 def _oracle_units(w: dict):
     """Endless stream of small pieces of the workload for the CPU oracle, each a
     call returning the point-steps it advanced, and a description of the sample:
@@ -512,13 +545,13 @@ class RingRunner:
         form = last["form"]
         launches = max(1, last["launches"])
         name = {"plain": "k_plain_f64" if self.w["dtype"] == "f64" else "k_plain_f32c", "persist": "k_persist",
-                "tblock": "k_tblock", "cluster": "k_cluster", "persist_tb": "k_batch"}[form]
+                "tblock": "k_tblock", "cluster": "k_cluster", "persist_tb": "k_wave"}[form]
         src = {"k_plain_f64": "k_plain.cu", "k_plain_f32c": "k_plain.cu", "k_persist": "k_persist.cu",
-               "k_tblock": "k_tblock.cu", "k_cluster": "k_cluster.cu", "k_batch": "k_batch.cu"}[name]
+               "k_tblock": "k_tblock.cu", "k_cluster": "k_cluster.cu", "k_wave": "k_wave.cu"}[name]
         srcs = [f"paper_2307_01117_gb300/csrc/{src}", "paper_2307_01117_gb300/csrc/stencil_ops.cuh"]
-        if name in ("k_tblock", "k_cluster", "k_batch"):
+        if name in ("k_tblock", "k_cluster", "k_wave"):
             srcs.append("paper_2307_01117_gb300/csrc/tb_core.cuh")
-        if name in ("k_tblock", "k_batch"):
+        if name in ("k_tblock", "k_wave"):
             srcs.append("paper_2307_01117_gb300/csrc/dp_emul.cuh")
         steps_per_launch = self.nt / launches
         elem = 8.0 if self.w["dtype"] == "f64" else 4.0
@@ -532,7 +565,7 @@ class RingRunner:
         return {"kernel": name, "src": srcs, "launches": launches, "launch_ms": statistics.mean(run_ms) / launches,
                 "point_steps_per_launch": self.n * steps_per_launch, "alg_bytes_per_launch": alg_bytes,
                 "form": form, "T": last["T"], "segments": last["segments"] if form != "plain" else None,
-                "emul_share": self.H.heat_get_emulation(self.h.ctx) if form == "tblock" else 0,
+                "emul_share": self.H.heat_get_emulation(self.h.ctx) if form in ("tblock", "persist_tb") else 0,
                 "r_pow2": is_pow2(r),
                 # FP64-unit operations per point-step: for r = 2^k every form but the strided
                 # temporal-blocking layout multiplies by moving the exponent on the integer pipes
@@ -555,7 +588,7 @@ class RingRunner:
 class BatchRunner:
     """Many rings in one batch: a step restores their initial states and runs one
     batch launch that advances every ring its nt steps."""
-    E2E_COPIES = "in series with the steps"
+    E2E_COPIES = "beside the launches: two batches on two streams take the steps in turn"
 
     def __init__(self, args, w, H, torch, local, stream):
         from paper_2307_01117_gb300 import workloads
@@ -574,7 +607,7 @@ class BatchRunner:
             H.heat_batch_set_emulation(self.b, args.emul)
         if args.T:
             H.heat_batch_set_tuning(self.b, args.T, 0)
-            self.tuned = (args.T, 16384)
+            self.tuned = (args.T, 0)
         else:
             self.tuned = H.heat_batch_autotune(self.b)
         H.heat_batch_save(self.b)
@@ -590,29 +623,57 @@ class BatchRunner:
         H.heat_batch_sync(self.b)
 
     def e2e_prepare(self):
-        torch = self.torch
+        # two batches on two streams take the steps in turn: while one runs its
+        # launch, the other's results are read back and its next inputs copied
+        # in; an event keeps the two batches' launches in order on the device
+        torch, H = self.torch, self.H
         self.host_in = [torch.from_numpy(u).pin_memory().numpy() for u in self.inits]
-        self.host_out = [torch.empty(s.n, dtype=torch.float64, pin_memory=True).numpy() for s in self.specs]
+        self.host_out = [[torch.empty(s.n, dtype=torch.float64, pin_memory=True).numpy() for s in self.specs]
+                         for _ in range(2)]
+        if getattr(self, "b2", None) is None:
+            self.stream2 = torch.cuda.Stream()
+            dt = H.HEAT_F64 if self.w["dtype"] == "f64" else H.HEAT_F32C
+            self.b2 = H.heat_batch_create(sum(s.n + 64 for s in self.specs), dt)
+            H.heat_batch_set_stream(self.b2, self.stream2)
+            H.heat_batch_set_tuning(self.b2, *self.tuned)
+            if self.args.emul >= 0:
+                H.heat_batch_set_emulation(self.b2, self.args.emul)
+            self.ids2 = []
+        self.pipe = [[self.b, self.stream, self.ids], [self.b2, self.stream2, self.ids2]]
+        self.done = [torch.cuda.Event(), torch.cuda.Event()]
 
     def e2e_run(self, k):
-        for _ in range(k):
-            self._e2e_step()
+        H, prev = self.H, None
+        for i in range(k):
+            x = i & 1
+            b, s, ids = self.pipe[x]
+            for rid in ids:
+                H.heat_batch_remove(b, rid)
+            # host -> device, beside the other batch's launch
+            ids[:] = [H.heat_batch_add(b, sp.nx, sp.np_, sp.r, 1.0, 1.0, sp.nt, u) for sp, u in
+                      zip(self.specs, self.host_in)]
+            if prev is not None:
+                s.wait_event(self.done[prev])
+            H.heat_batch_run(b, 0)
+            self.done[x].record(s)
+            if prev is not None:
+                self._e2e_finish(prev)                # device -> host, beside this batch's launch
+            prev = x
+        self._e2e_finish(prev)
+        self.ids = self.pipe[0][2]
 
-    def _e2e_step(self):
-        H = self.H
-        for rid in self.ids:
-            H.heat_batch_remove(self.b, rid)
-        self.ids = [H.heat_batch_add(self.b, s.nx, s.np_, s.r, 1.0, 1.0, s.nt, u) for s, u in
-                    zip(self.specs, self.host_in)]
-        H.heat_batch_run(self.b, 0)
-        for rid, s, out in zip(self.ids, self.specs, self.host_out):
-            H.heat_batch_get(self.b, rid, s.n, out)
+    def _e2e_finish(self, x):
+        b, _, ids = self.pipe[x]
+        for rid, sp, out in zip(ids, self.specs, self.host_out[x]):
+            self.H.heat_batch_get(b, rid, sp.n, out)
 
     def e2e_bytes(self):
         return self.n_total * 8, self.n_total * 8
 
     def e2e_agree(self):
-        return None
+        """Both batches advanced the same inputs: their read-back states agree bitwise."""
+        return all(np.array_equal(a.view(np.uint64), c.view(np.uint64))
+                   for a, c in zip(self.host_out[0], self.host_out[1]))
 
     def kernel_info(self, run_ms):
         T = self.tuned[0]
@@ -635,11 +696,13 @@ class BatchRunner:
         return {"workload": self.args.workload, "rings": len(self.specs), "points": self.n_total,
                 "point_steps": self.point_steps, "n_min": min(ns), "n_max": max(ns),
                 "nt_range": [min(s.nt for s in self.specs), max(s.nt for s in self.specs)],
-                "tuning": {"T": self.tuned[0], "seg_points": self.tuned[1]},
+                "tuning": {"T": self.tuned[0], "window_points": self.tuned[1]},
                 "l2": "inputs larger than L2 (no flush needed)"}
 
     def close(self):
         self.H.heat_batch_destroy(self.b)
+        if getattr(self, "b2", None) is not None:
+            self.H.heat_batch_destroy(self.b2)
 
 
 class PrecisionRunner(RingRunner):
@@ -767,7 +830,8 @@ class ServeRunner:
 # Sub-records of the default line: the plain one-step-per-launch kernel on the same
 # ring, and a short serving window
 
-def plain_subrecord(args, w, H, torch, local, stream, sms: int, pk: dict, steps: int = 2) -> dict:
+def plain_subrecord(args, w, H, torch, local, stream, sms: int, pk: dict, probe: dict | None,
+                    steps: int = 2) -> dict:
     """The same ring advanced by the plain form (one launch per step): GLUP/s with
     its HBM fraction (16 B per point-step, binary64) and its FP64-unit fraction,
     timed like the headline (CUDA events around heat_run, one warm-up step that
@@ -793,11 +857,14 @@ def plain_subrecord(args, w, H, torch, local, stream, sms: int, pk: dict, steps:
     dp_ops = 3 if (args.arith == "exact" and is_pow2(r)) else DP_OPS[args.arith]
     f_peak = 2.0 * sms * pk["sm_max_mhz"] * 1e6 / dp_ops / 1e9
     hbm_gbs = glups * 2 * elem
+    f_meas = (1e-9 / (1.0 / probe["dfma_lane_ops_per_s"] + (dp_ops - 1) / probe["dadd_lane_ops_per_s"])
+              if probe else None)
     return {"kernel": "k_plain_f64" if w["dtype"] == "f64" else "k_plain_f32c", "form": "plain",
             "value": glups, "unit": UNIT, "steps": steps, "launches_per_step": launches,
             "hbm": {"achieved": hbm_gbs, "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": hbm_gbs / pk["hbm_gbs"],
                     "bytes_per_point_step": 2 * elem},
             "fp64_unit": {"achieved": glups, "peak": f_peak, "unit": "GLUP/s", "frac": glups / f_peak,
+                          "peak_measured": f_meas, "frac_measured": glups / f_meas if f_meas else None,
                           "fp64_ops_per_point_step": dp_ops} if w["dtype"] == "f64" else None,
             "headline_over_plain": None}
 
@@ -844,6 +911,8 @@ def main() -> int:
     ap.add_argument("--rate", type=float, default=0.0, help="serving workloads: arrivals per second")
     ap.add_argument("--duration", type=float, default=0.0, help="serving workloads: window length (s)")
     ap.add_argument("--tick", type=int, default=256, help="serving workloads: steps per tick")
+    ap.add_argument("--cpu-report", action="store_true",
+                    help="print the CPU baselines on the paper-shaped configurations (no GPU) and exit")
     ap.add_argument("--no-plain", action="store_true", help="leave out the plain-form sub-record")
     ap.add_argument("--no-serving", action="store_true", help="leave out the serving sub-record")
     args = ap.parse_args()
@@ -858,6 +927,10 @@ def main() -> int:
 
     if args.impl == "reference":
         run_reference(args, w, rank)
+        return 0
+    if args.cpu_report:
+        if rank == 0:
+            print(json.dumps({"cpu_report": cpu_report()}), flush=True)
         return 0
 
     import torch
@@ -907,6 +980,13 @@ def main() -> int:
     ki = runner.kernel_info(run_ms)
     pk = peaks()
     sms = torch.cuda.get_device_properties(local).multi_processor_count
+    # measured issue rates of the FP64 unit and the integer ALU pipes (probe
+    # kernels, CUDA events), beside the nominal 2 and 64 lane-ops/clk/SM
+    probe = None
+    if w["dtype"] == "f64" and w["kind"] != "serve":
+        probe = H.heat_probe_pipes(stream)
+        probe["nominal_dp_lane_ops_per_s"] = 2.0 * sms * pk["sm_max_mhz"] * 1e6
+        probe["nominal_alu_lane_ops_per_s"] = 64.0 * sms * pk["sm_max_mhz"] * 1e6
     launch_s = ki["launch_ms"] * 1e-3
     hbm = ki["alg_bytes_per_launch"] / launch_s / 1e9
     roof_hbm = {"bound": "hbm", "achieved": hbm, "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": hbm / pk["hbm_gbs"],
@@ -927,12 +1007,20 @@ def main() -> int:
         share = ki.get("emul_share", 0)
         roofline = {"bound": "alu", "achieved": achieved, "unit": "GLUP/s", "fp64_unit_peak": f_peak,
                     "fp64_ops_per_point_step": dp_ops, "emul_share_of_32": share}
+        # the same ceilings from the probe's measured rates: one fused multiply-add
+        # and dp_ops - 1 adds (or multiplies, issued like adds) per point-step
+        f_meas = 1e-9 / (1.0 / probe["dfma_lane_ops_per_s"] + (dp_ops - 1) / probe["dadd_lane_ops_per_s"])
+        roofline["fp64_unit_peak_measured"] = f_meas
         if share:
             a_ops = alu_ops("pow2" if ki.get("r_pow2") else "general")
             i_peak = 64.0 * sms * sm_hz / a_ops / 1e9 if a_ops else None
             peak = f_peak + i_peak if i_peak else None
+            i_meas = probe["alu_lane_ops_per_s"] / a_ops / 1e9 if a_ops else None
             roofline.update({
                 "peak": peak, "frac": achieved / peak if peak else None, "int_pipes_peak": i_peak,
+                "int_pipes_peak_measured": i_meas,
+                "peak_measured": f_meas + i_meas if i_meas else None,
+                "frac_measured": achieved / (f_meas + i_meas) if i_meas else None,
                 "alu_inst_per_int_point_step": a_ops,
                 "peak_src": f"FP64 unit: 2 DP ops/clk/SM x {sms} SMs x {pk['sm_max_mhz']:.0f} MHz / "
                             f"{dp_ops} per point-step, plus ALU pipes: 64 lanes/clk/SM x {sms} SMs x "
@@ -940,7 +1028,7 @@ def main() -> int:
                             f"(ncu-measured, profiles/alu_ops.json)"})
         else:
             roofline.update({
-                "peak": f_peak, "frac": achieved / f_peak,
+                "peak": f_peak, "frac": achieved / f_peak, "peak_measured": f_meas, "frac_measured": achieved / f_meas,
                 "peak_src": f"FP64 unit: 2 DP ops/clk/SM x {sms} SMs x {pk['sm_max_mhz']:.0f} MHz max SM clock "
                             f"/ {dp_ops} DP ops per point-step (GB300 nominal 1.25 TFLOP/s FP64)"})
     else:
@@ -977,7 +1065,7 @@ def main() -> int:
     # serving window beside the headline (outside its timed region)
     plain = serving = None
     if w["kind"] == "ring" and w["dtype"] == "f64" and not args.no_plain and ki["form"] != "plain":
-        plain = plain_subrecord(args, w, H, torch, local, stream, sms, pk)
+        plain = plain_subrecord(args, w, H, torch, local, stream, sms, pk, probe)
         plain["headline_over_plain"] = value / plain["value"]
     if args.workload == DEFAULT_WORKLOAD and not args.no_serving:
         serving = serving_subrecord(stream)
@@ -1000,6 +1088,8 @@ def main() -> int:
             "e2e": e2e,
             "gpu_launches": launches, "clocks": clk,
         }
+        if probe is not None:
+            line["pipe_probe"] = probe
         if plain is not None:
             line["plain"] = plain
         if serving is not None:

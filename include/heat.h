@@ -77,8 +77,10 @@ typedef enum {
                             swaps ghost values with its neighbours through
                             device-memory flag queues (Section 2's SPSC queues) */
   HEAT_FORM_TBLOCK = 2,  /* temporal blocking: T steps per register-resident tile */
-  HEAT_FORM_AUTO = 3,    /* library picks: HEAT_FORM_CLUSTER for every ring the
-                            cluster form takes (measured fastest there),
+  HEAT_FORM_AUTO = 3,    /* library picks (measured fastest for each range):
+                            HEAT_FORM_CLUSTER for every ring the cluster form
+                            takes, HEAT_FORM_PERSIST_TB for binary64 rings under
+                            the exact reading from 2^19 to 2^26 points,
                             HEAT_FORM_TBLOCK otherwise */
   HEAT_FORM_CLUSTER = 4, /* small rings (up to 16 x 4 windows of output, about
                             31000 binary64 points at T = 8): one thread-block
@@ -88,11 +90,12 @@ typedef enum {
                             distributed shared memory, one cluster barrier per
                             block of T steps */
   HEAT_FORM_PERSIST_TB = 5 /* persistent temporal blocking: one launch for all
-                            nt steps; the ring is cut into segments that advance
-                            T steps at a time, each waiting (acquire/release
-                            flags, bounded) until it and its two neighbours
-                            finished the previous block -- the segmented
-                            algorithm of Section 2 with T-wide ghost zones */
+                            nt steps; the ring is cut into warp-sized tiles that
+                            advance T steps at a time, each waiting (acquire/
+                            release completion counters, bounded) until it and
+                            its two neighbours finished the previous block --
+                            the segmented algorithm of Section 2 with T-wide
+                            ghost zones, no launch boundary between blocks */
 } heat_form;
 
 /* Rounding reading of Eq. 2 for HEAT_F64 (the paper states no order). */
@@ -158,11 +161,12 @@ int heat_set_stream(heat_ctx *c, void *cuda_stream);
  * that is not a power of two), else 12 when part of the tiles run on the
  * integer pipes, else 8 below 2^22 points and 4 from 2^22 points; in the
  * cluster form 16, or 8 for rings that one cluster holds only at that depth;
- * in the persistent temporal-blocking form 12).  T is ignored by the one-step
- * forms.
+ * in the persistent temporal-blocking form 32 for HEAT_F32C, for HEAT_F64 8
+ * below 2^21 points and 16 from 2^21).  T is ignored by the one-step forms.
  * HEAT_FORM_AUTO (the default) is HEAT_FORM_CLUSTER for binary64 rings of at
  * most 6144 points and binary32 rings that one thread-block cluster holds,
- * else HEAT_FORM_TBLOCK. */
+ * HEAT_FORM_PERSIST_TB for binary64 rings under the exact reading from 2^19 to
+ * 2^26 points, else HEAT_FORM_TBLOCK. */
 int heat_set_form(heat_ctx *c, int form, int T);
 
 /* Segmentation of the persistent forms: 0 = library default (near-equal
@@ -270,12 +274,13 @@ int heat_inject_stall(heat_ctx *c, int32_t segment, int64_t from_step);
  * result is bitwise the one heat_run gives for it alone (binary64) or the one
  * the temporal-blocking form gives with the same block depth (HEAT_F32C).
  *
- * The batch's kernel runs over a work table of units (level b, ring, segment):
- * a ring of n points is cut into segments; level b advances a segment by T steps
- * (fewer at the ring's last level); units are claimed in level order, and a unit
- * waits (bounded) until its segment and the two neighbouring segments have
- * finished level b-1.  T and the segment size come from heat_batch_set_tuning
- * or heat_batch_autotune.
+ * The batch's kernel runs over a work table of units (level b, ring, tile): a
+ * ring of n points is cut into near-equal warp tiles (of at most the warp
+ * window minus 2T points); level b advances a tile by T steps (fewer at the
+ * ring's last level); warps claim units in level order, and a unit waits
+ * (bounded) until its tile and the two neighbouring tiles have finished level
+ * b-1.  T and the warp window come from heat_batch_set_tuning or
+ * heat_batch_autotune.
  * ------------------------------------------------------------------------- */
 typedef struct heat_batch heat_batch; /* opaque, library-owned */
 
@@ -325,17 +330,20 @@ int heat_batch_get_device(heat_batch *b, int32_t ring_id, double *dev_u, int64_t
  * is queued behind it on the same stream. */
 int heat_batch_remove(heat_batch *b, int32_t ring_id);
 
-/* Temporal block depth T (1..64) and target segment length in points (>= 512);
- * 0 keeps the current value (defaults: T = 8 for binary64, 32 for HEAT_F32C;
- * segments of 16384 points). */
-int heat_batch_set_tuning(heat_batch *b, int T, int64_t seg_points);
+/* Temporal block depth T (1..64) and warp window in points: the kernel has
+ * three windows, 128, 256 and 512 binary64 points (256, 512 and 1024 binary32
+ * points); a request takes the widest of them not above it, at least the
+ * narrowest.  0 keeps the current value (defaults: T = 8 for binary64, 32 for
+ * HEAT_F32C; the widest window).  A run widens the window while a tile would
+ * keep fewer than 2T output points. */
+int heat_batch_set_tuning(heat_batch *b, int T, int64_t window_points);
 
-/* Pick T and the segment length by timing one level of the current rings for
- * each candidate (the rings' states are not changed: one level only writes the
- * idle buffer).  The choice is cached in the file named by the environment
- * variable HEAT_TUNE_CACHE, if set, keyed by dtype and a coarse description of
- * the batch.  Synchronous. */
-int heat_batch_autotune(heat_batch *b, int *T_out, int64_t *seg_points_out);
+/* Pick T and the warp window by timing one level of the current rings for each
+ * candidate (the rings' states are not changed: one level only writes the idle
+ * buffer).  The choice is cached in the file named by the environment variable
+ * HEAT_TUNE_CACHE, if set, keyed by dtype and a coarse description of the
+ * batch.  Synchronous. */
+int heat_batch_autotune(heat_batch *b, int *T_out, int64_t *window_points_out);
 
 /* Queue subsequent work on cuda_stream (NULL: the batch's own stream). */
 int heat_batch_set_stream(heat_batch *b, void *cuda_stream);
@@ -360,7 +368,7 @@ int heat_batch_set_emulation(heat_batch *b, int share);
  * HEAT_ETIMEOUT at the next heat_batch_sync / heat_batch_get. */
 int heat_batch_set_wait_limit(heat_batch *b, int64_t ns);
 
-/* Test hook (host-side fault injection): in later runs, segment `segment` of
+/* Test hook (host-side fault injection): in later runs, tile `segment` of
  * ring `ring_id` stops publishing its completion from level `from_level` on,
  * so the units that depend on it run out of their bounded waits and the run
  * ends with HEAT_ETIMEOUT; every kernel returns normally.  A ring id that is
@@ -411,6 +419,17 @@ int heat_batch_info(const heat_batch *b, int32_t *live_rings, int64_t *largest_f
  * steps queued before it still run and dev_u is undefined. */
 int heat_run_noalloc(const double *dev_u0, double *dev_u, int64_t n, double k, double dt, double dx,
                      int64_t nt, int arith, void *cuda_stream);
+
+/* Measured issue rates of the engines the binary64 update runs on, for roofline
+ * denominators (the paper has no counterpart: it measures CPUs).  Three probe
+ * kernels run on the current device, on cuda_stream (NULL = default stream),
+ * each on a full-occupancy grid of independent dependency chains, timed with
+ * CUDA events after one untimed launch: binary64 fused multiply-adds, binary64
+ * adds, and 32-bit bitwise majorities (LOP3, ALU-pipe instructions).  Results are
+ * lane operations per second; any pointer may be NULL.  Synchronous; allocates
+ * and frees a small device buffer.  HEAT_ECUDA if a launch fails. */
+int heat_probe_pipes(void *cuda_stream, double *dfma_lane_ops_per_s, double *dadd_lane_ops_per_s,
+                     double *alu_lane_ops_per_s);
 
 /* Static text for a status code. */
 const char *heat_strerror(int code);

@@ -44,7 +44,7 @@ void free_ctx(heat_ctx *c) {
   if (c->xstage) cudaFree(c->xstage);
   if (c->tile_counter) cudaFree(c->tile_counter);
   if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
-  heat::free_persist_tb(c);
+  heat::free_wave(c);
   if (c->own_stream) cudaStreamDestroy(c->own_stream);
   free(c);
 }
@@ -303,6 +303,8 @@ int heat_run(heat_ctx *c, int64_t nt) {
     const int Tc = c->T > 0 ? c->T : (c->dtype == HEAT_F32C ? 32 : 16);
     const int64_t limit = c->dtype == HEAT_F32C ? heat::cluster_max_points(c, Tc) : 6144;
     form = c->geo.N <= limit && c->geo.N <= heat::cluster_max_points(c, Tc) ? HEAT_FORM_CLUSTER : HEAT_FORM_TBLOCK;
+    // mid-size binary64 rings: dependency-driven temporal blocking in one launch
+    if (form == HEAT_FORM_TBLOCK && heat::wave_preferred(c)) form = HEAT_FORM_PERSIST_TB;
   }
   c->last_form = form;
   c->last_T = 1;

@@ -44,8 +44,6 @@ struct Geometry {
 
 }  // namespace heat
 
-struct heat_batch;
-
 struct heat_ctx {
   heat::Geometry geo;
   double r;          // k*dt/(dx*dx), binary64
@@ -78,7 +76,9 @@ struct heat_ctx {
   int emul_auto;                 // share chosen per ring (heat_set_emulation(c, -1))
   int split_level;               // per-point split of the binary64 update between FP64 unit and integer pipes
   int tb_layout;                 // temporal-blocking register layout: 0 strided (TMA-staged), 1 contiguous
-  heat_batch *ptb;               // work-table state of the persistent temporal-blocking form (lazy)
+  unsigned *wave_done;           // persistent temporal blocking, device: levels finished per tile (lazy)
+  int64_t wave_cap;              // capacity of wave_done
+  unsigned long long *wave_counter;  // its unit counter, device (lazy)
   // CUDA graph of the last multi-launch run (plain / temporal blocking), replayed
   // when the next run has the same key
   int graphs;                    // 1: capture and replay multi-launch runs
@@ -107,7 +107,10 @@ int tblock_default_T(const heat_ctx *c);
 unsigned tblock_emul_mask(const heat_ctx *c);
 int run_cluster(heat_ctx *c, int64_t nt);
 int run_persist_tb(heat_ctx *c, int64_t nt);
-void free_persist_tb(heat_ctx *c);
+int run_wave(heat_ctx *c, int64_t nt, int T);
+int wave_default_T(const heat_ctx *c);
+bool wave_preferred(const heat_ctx *c);
+void free_wave(heat_ctx *c);
 int64_t cluster_max_points(const heat_ctx *c, int T);
 int sum_state(heat_ctx *c, double *out);
 int convert_f64_to_state(heat_ctx *c, const double *dev_src, void *dev_dst, int64_t n);

@@ -4,27 +4,26 @@
 //
 // Work table (built on the host for each run, rings sorted by the number of
 // T-step levels they need, longest first):
-//   ring i: arena offset, n points, steps this run, nseg segments, r;
-//   units (level b, ring i, segment j) are numbered level-major, so the rings
+//   ring i: arena offset, n points, steps this run, ntiles warp tiles, r;
+//   units (level b, ring i, tile j) are numbered level-major, so the rings
 //   active at level b are a prefix of the sorted list and a unit number decodes
-//   with two binary searches (over the per-level and per-ring prefix sums).
-// A CTA claims the next unit from a launch-wide counter.  Unit (b, i, j) reads
-// the ring's state at time bT from one arena buffer and writes time
-// bT + steps_b into the other; before that it waits (bounded) until segments
-// j-1, j, j+1 of ring i have finished level b-1.  Units are numbered level-major
-// and claimed in increasing order, so every unit a CTA waits for has a smaller
-// number and was claimed earlier by a CTA that is running it; the CTA holding
-// the smallest unfinished unit therefore never waits on anything unfinished,
-// and the launch makes progress with any number of resident CTAs.  No
-// co-residency is needed: the kernel is an ordinary launch, and two batches
-// (binary64 and binary32) can share the GPU.  The same wait covers the
-// write-after-read hazard on the output buffer, which level b-1's neighbours
-// read.
+//   with two searches (over the per-level and per-ring prefix sums).
+// A warp claims a chunk of consecutive units from a launch-wide counter.  Unit
+// (b, i, j) advances tile j of ring i from time bT to bT + steps_b with the
+// register-resident temporal-blocking core (wave_core.cuh), after waiting
+// (bounded) until tiles j-1, j, j+1 of the ring have finished level b-1.
+// Units are numbered level-major and claimed in increasing order, and a warp
+// runs its chunk in order, so every unit a warp waits for has a smaller number
+// and was claimed earlier by a warp that is running it; the warp holding the
+// smallest unfinished unit therefore never waits on anything unfinished, and
+// the launch makes progress with any number of resident CTAs.  No co-residency
+// is needed: the kernel is an ordinary launch, and two batches (binary64 and
+// binary32) can share the GPU.  The same wait covers the write-after-read
+// hazard on the output buffer, which level b-1's neighbours read.
 //
-// Within a unit the CTA's warps cover the segment with register-resident
-// temporal-blocking windows (tb_core.cuh); windows wrap around the ring's ends
-// with modular indices.  Every point is computed from the same operands as in
-// the single-ring forms, so each ring's result is bitwise its solo result.
+// Windows wrap around the ring's ends with modular indices.  Every point is
+// computed from the same operands as in the single-ring forms, so each ring's
+// result is bitwise its solo result.
 #include <math.h>
 #include <stdint.h>
 #include <stdio.h>
@@ -37,7 +36,7 @@
 #include <string>
 #include <vector>
 
-#include "tb_core.cuh"
+#include "wave_core.cuh"
 
 static constexpr int64_t kAlignPointsHost = 64;  // ring placement granularity in the arena (points)
 
@@ -45,20 +44,20 @@ namespace heat {
 namespace {
 
 constexpr int kBWarps = 4;
-constexpr long long kMaxSpins = 1LL << 26;
+constexpr int kChunk = 4;  // consecutive units per claim
 
 struct BRing {
   int64_t off;        // arena offset in points
   int64_t n;          // ring length
   int64_t steps;      // steps this run
-  int64_t nseg;       // segments
-  int64_t done_base;  // index of segment 0's done counter
+  int64_t nseg;       // warp tiles
+  int64_t done_base;  // index of tile 0's done counter
   double r;
   float rf;
   int parity;         // arena buffer holding the state at the start of the run
   emul::MulX mx;      // r for the integer-pipe tiles (binary64, exact reading)
   int dom_lo, dom_hi; // their input screen for T steps (empty: dom_lo > dom_hi)
-  unsigned emul_mask; // bit (tile mod 32) set: that tile of a unit on the integer pipes
+  unsigned emul_mask; // bit (tile mod 32) set: that tile on the integer pipes
   int p2_hi_add, p2_hi_xor;  // r = +-2^k: screened FP64-unit tiles move the product's exponent
 };
 
@@ -71,186 +70,90 @@ struct BatchArgs {
   const int32_t *active;  // rings active at each level (L)
   int L;
   int T;
-  int dual;  // binary64 under the library's share: two-ended tile claiming within units
+  int dual;  // binary64 under the library's share: integer-pipe warps and FP64-unit warps
   unsigned *done;
   unsigned long long *counter;
   DevStatus *st;
   long long wait_ns;
-  int inj_ring;        // test hook: table index of a ring whose segment stops publishing (-1: none)
+  int inj_ring;        // test hook: table index of a ring whose tile stops publishing (-1: none)
   long long inj_seg;
   long long inj_level;
 };
 
-__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p) {
-  unsigned v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-
-__device__ __forceinline__ void st_release_u32(unsigned *p, unsigned v) {
-  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
-__device__ __forceinline__ unsigned long long now_ns() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-// Bounded wait until *p >= target; false (and the device status set) if it ran out.
-__device__ bool wait_done(const BatchArgs &a, const unsigned *p, unsigned target, int ring, long long level) {
-  if (ld_acquire_u32(p) >= target) return true;
-  const unsigned long long deadline = now_ns() + (unsigned long long)a.wait_ns;
-  unsigned ns = 32;
-  for (long long spin = 0; spin < kMaxSpins; ++spin) {
-    if (ld_acquire_u32(p) >= target) return true;
-    if (*(volatile int *)&a.st->abort) return false;
-    if (now_ns() > deadline) break;
-    __nanosleep(ns);
-    if (ns < 1024) ns <<= 1;
-  }
-  if (atomicCAS(&a.st->code, HEAT_OK, HEAT_ETIMEOUT) == HEAT_OK) {
-    a.st->segment = ring;
-    a.st->step = level;
-  }
-  atomicExch(&a.st->abort, 1);
-  return false;
-}
-
-// Largest index k in [lo, hi) with v[k] <= x (v nondecreasing, v[lo] <= x).
-__device__ __forceinline__ int64_t floor_index(const int64_t *v, int64_t lo, int64_t hi, int64_t x) {
+// Largest index k in [lo, hi) with v[k] <= x (v nondecreasing, v[lo] <= x),
+// found by the whole warp: each round every lane probes one of 32 evenly
+// spaced entries, so a round narrows the range 32-fold.
+__device__ __forceinline__ int64_t floor_index_warp(const int64_t *v, int64_t lo, int64_t hi, int64_t x, int lane) {
   while (hi - lo > 1) {
-    const int64_t mid = (lo + hi) >> 1;
-    if (v[mid] <= x) lo = mid; else hi = mid;
+    const int64_t step = (hi - lo + 31) / 32;
+    const int64_t k = lo + (int64_t)lane * step;
+    const unsigned m = __ballot_sync(tb::kFull, k < hi && __ldcg(v + k) <= x);
+    lo += (int64_t)(31 - __clz(m)) * step;  // the probes at or below x are a prefix of the lanes
+    hi = lo + step < hi ? lo + step : hi;
   }
   return lo;
 }
 
-template <int MODE>
-__global__ void __launch_bounds__(kBWarps * 32, MODE == 2 ? 3 : 6) k_batch(BatchArgs a) {  // MODE: 0 exact, 1 fused, 2 binary32
-  using P = tb::TBC<MODE>;  // contiguous per-lane ownership
-  using T = typename P::T;
-  constexpr int E = P::E;
-  constexpr int WIN = 32 * E;
-  __shared__ long long s_ring, s_level, s_lo, s_hi, s_steps, s_seg;
-  __shared__ int s_stop;
-  __shared__ unsigned long long s_tile;  // the unit's tiles are claimed by the CTA's warps (see below)
+template <int MODE, int EP>
+__global__ void __launch_bounds__(kBWarps * 32, MODE == 2 ? 1 : 8) k_batch(BatchArgs a) {  // MODE: 0 exact, 1 fused, 2 binary32
+  using T = typename tb::TBCx<MODE, EP>::T;
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
   const int64_t total = a.levp[a.L];
-  const int W = WIN - 2 * a.T;
-
+  const bool int_warp = MODE == 0 && a.dual && (((blockIdx.x ^ wib) & 1) != 0);
   for (;;) {
-    if (threadIdx.x == 0) {
-      const unsigned long long u = atomicAdd(a.counter, 1ull);
-      int stop = 0;
-      if ((int64_t)u >= total) {
-        stop = 1;
-      } else {
-        const int64_t b = floor_index(a.levp, 0, a.L, (int64_t)u);
-        const int64_t rel = (int64_t)u - a.levp[b];
-        const int64_t i = floor_index(a.segp, 0, a.active[b], rel);
-        const int64_t j = rel - a.segp[i];
-        const BRing R = a.rings[i];
-        if (b > 0) {
-          const int64_t jm = j == 0 ? R.nseg - 1 : j - 1, jp = j + 1 == R.nseg ? 0 : j + 1;
-          const unsigned tgt = (unsigned)b;
-          if (!(wait_done(a, a.done + R.done_base + jm, tgt, (int)i, b) &&
-                wait_done(a, a.done + R.done_base + j, tgt, (int)i, b) &&
-                wait_done(a, a.done + R.done_base + jp, tgt, (int)i, b)))
-            stop = 2;
-        }
-        s_ring = i;
-        s_level = b;
-        s_seg = j;
-        s_lo = (j * R.n) / R.nseg;
-        s_hi = ((j + 1) * R.n) / R.nseg;
-        const int64_t left = R.steps - b * a.T;
-        s_steps = left < a.T ? left : a.T;
-      }
-      s_stop = stop;
-      s_tile = 0;
+    unsigned long long u0 = 0;
+    int go = 1;
+    if (lane == 0) {
+      u0 = atomicAdd(a.counter, (unsigned long long)kChunk);
+      go = (int64_t)u0 < total && !wave::aborted(a.st);
     }
-    __syncthreads();
-    if (s_stop) break;  // uniform across the CTA
-    const BRing R = a.rings[s_ring];
-    const int par = R.parity ^ (int)(s_level & 1);
-    const T *src = (const T *)(par ? a.arena1 : a.arena0) + R.off;
-    T *dst = (T *)(par ? a.arena0 : a.arena1) + R.off;
-    const int64_t lo = s_lo, hi = s_hi, n = R.n;
-    const int steps = (int)s_steps;
-    const int64_t ntile = (hi - lo + W - 1) / W;
-    // Binary64 rings under the library's share: two-ended claiming within the
-    // unit (integer-pipe warps from the end, FP64-unit warps from the start,
-    // one 64-bit shared counter), so the split follows the engines' speeds.
-    // Otherwise tiles in order, R.emul_mask choosing their engine.
-    const bool dual = MODE == 0 && a.dual && R.emul_mask != 0u;
-    const bool int_warp = dual && (((blockIdx.x ^ wib) & 1) != 0);
-    for (;;) {
-      unsigned long long tc = 0;
-      if (lane == 0) tc = atomicAdd(&s_tile, int_warp ? (1ull << 32) : 1ull);
-      tc = __shfl_sync(0xffffffffu, tc, 0);
-      int64_t t;
-      bool int_tile;
-      if (dual) {
-        const int64_t f = (int64_t)(tc & 0xffffffffull), b = (int64_t)(tc >> 32);
-        if (f + b >= ntile) break;
-        t = int_warp ? ntile - 1 - b : f;
-        int_tile = int_warp;
+    u0 = __shfl_sync(tb::kFull, u0, 0);
+    if (!__shfl_sync(tb::kFull, go, 0)) break;
+    const int64_t u1 = (int64_t)u0 + kChunk < total ? (int64_t)u0 + kChunk : total;
+    int64_t b = -1, i = 0, j = 0, lev_end = 0, ring_end = 0;
+    bool stop = false;
+    for (int64_t u = (int64_t)u0; u < u1; ++u) {
+      if (u < lev_end && u < ring_end) {
+        ++j;  // the next tile of the same ring and level
       } else {
-        t = (int64_t)tc;
-        if (t >= ntile) break;
-        int_tile = MODE == 0 && ((R.emul_mask >> (unsigned)(t & 31)) & 1u);
+        b = floor_index_warp(a.levp, 0, a.L, u, lane);
+        const int64_t rel = u - __ldcg(a.levp + b);
+        i = floor_index_warp(a.segp, 0, __ldcg(a.active + b), rel, lane);
+        j = rel - __ldcg(a.segp + i);
+        lev_end = __ldcg(a.levp + b + 1);
+        ring_end = u - j + __ldcg(a.segp + i + 1) - __ldcg(a.segp + i);
       }
-      const int64_t ws = lo + t * W - a.T;
-      typename P::Reg reg;
-      const bool inside = ws >= 0 && ws + WIN <= n;
-#pragma unroll
-      for (int k = 0; k < E; ++k) {
-        int64_t g = ws + E * lane + k;
-        if (!inside) {
-          g %= n;
-          if (g < 0) g += n;
-        }
-        P::load(reg, k, __ldcg(src + g));
+      const BRing &R = a.rings[i];
+      const int64_t nseg = R.nseg, base = R.done_base;
+      if (b > 0 && !wave::wait_neighbours(a.done + base, nseg, j, (unsigned)b, a.wait_ns, a.st, (int)i, lane)) {
+        stop = true;
+        break;
       }
-      bool dp = true;
+      __syncwarp();
+      int64_t lo, hi;
+      wave::tile_bounds(R.n, nseg, j, lo, hi);
+      const int par = R.parity ^ (int)(b & 1);
+      const T *src = (const T *)(par ? a.arena1 : a.arena0) + R.off;
+      T *dst = (T *)(par ? a.arena0 : a.arena1) + R.off;
+      const int64_t left = R.steps - b * a.T;
+      const int steps = (int)(left < a.T ? left : a.T);
+      bool int_tile = false, p2 = false;
+      wave::Engine e;
       if constexpr (MODE == 0) {
-        if (int_tile || R.mx.pow2) {
-          bool ok = true;
-#pragma unroll
-          for (int k = 0; k < E; ++k)
-            ok &= emul::in_domain((uint64_t)__double_as_longlong(P::store(reg, k)), R.dom_lo, R.dom_hi);
-          if (__all_sync(0xffffffffu, ok)) {
-            if (!int_tile)  // r = +-2^k on the FP64 unit: the product moves the exponent
-              for (int s = 0; s < steps; ++s) P::step_p2(reg, R.p2_hi_add, R.p2_hi_xor);
-            else if (R.mx.pow2 && !R.mx.neg)
-              P::template steps_x<true, false>(reg, steps, R.mx);
-            else if (R.mx.pow2)
-              P::template steps_x<true, true>(reg, steps, R.mx);
-            else if (!R.mx.neg)
-              P::template steps_x<false, false>(reg, steps, R.mx);
-            else
-              P::template steps_x<false, true>(reg, steps, R.mx);
-            dp = false;
-          }
-        }
+        int_tile = a.dual && R.emul_mask != 0u ? int_warp : ((R.emul_mask >> (unsigned)(j & 31)) & 1u) != 0;
+        p2 = R.mx.pow2 != 0;
+        e.mx = R.mx;
+        e.dom_lo = R.dom_lo;
+        e.dom_hi = R.dom_hi;
+        e.p2_hi_add = R.p2_hi_add;
+        e.p2_hi_xor = R.p2_hi_xor;
       }
-      if (dp)
-        for (int s = 0; s < steps; ++s) P::step(reg, lane, R.r, R.rf);
-      const int64_t out_hi = lo + (t + 1) * W < hi ? lo + (t + 1) * W : hi;
-#pragma unroll
-      for (int k = 0; k < E; ++k) {
-        const int i = E * lane + k;
-        const int64_t g = ws + i;
-        if (i >= a.T && i < WIN - a.T && g < out_hi) dst[g] = P::store(reg, k);
-      }
+      wave::advance_tile<MODE, EP>(src, dst, R.n, lo, hi, a.T, steps, R.r, R.rf, int_tile, p2, e, lane);
+      if (!(i == a.inj_ring && j == a.inj_seg && b >= a.inj_level))
+        wave::publish(a.done + base + j, (unsigned)(b + 1), lane);
     }
-    __syncthreads();
-    if (threadIdx.x == 0 && !(s_ring == a.inj_ring && s_seg == a.inj_seg && s_level >= a.inj_level)) {
-      __threadfence();
-      st_release_u32(a.done + R.done_base + s_seg, (unsigned)(s_level + 1));
-    }
+    if (stop) break;
   }
 }
 
@@ -264,17 +167,36 @@ __global__ void k_b_f32_to_f64(const float *__restrict__ s, double *__restrict__
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += st) d[i] = (double)s[i];
 }
 
-template <int MODE>
-cudaError_t launch_batch(BatchArgs &a, int grid, cudaStream_t st) {
-  k_batch<MODE><<<grid, kBWarps * 32, 0, st>>>(a);
+template <int MODE, int EP>
+cudaError_t launch_batch_ep(BatchArgs &a, int grid, cudaStream_t st) {
+  k_batch<MODE, EP><<<grid, kBWarps * 32, 0, st>>>(a);
   return cudaGetLastError();
 }
 
-template <int MODE>
-int per_sm_ctas() {
+template <int MODE, int EP>
+int per_sm_ctas_ep() {
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch<MODE>, kBWarps * 32, 0) != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch<MODE, EP>, kBWarps * 32, 0) != cudaSuccess)
+    return 0;
   return per_sm;
+}
+
+// Warp windows the batch kernel is built for (points per lane, by dtype).
+template <int MODE>
+constexpr int kEps[3] = {MODE == 2 ? 8 : 4, MODE == 2 ? 16 : 8, MODE == 2 ? 32 : 16};
+
+template <int MODE>
+cudaError_t launch_batch(BatchArgs &a, int ep, int grid, cudaStream_t st) {
+  return ep == kEps<MODE>[0]   ? launch_batch_ep<MODE, kEps<MODE>[0]>(a, grid, st)
+         : ep == kEps<MODE>[1] ? launch_batch_ep<MODE, kEps<MODE>[1]>(a, grid, st)
+                               : launch_batch_ep<MODE, kEps<MODE>[2]>(a, grid, st);
+}
+
+template <int MODE>
+int per_sm_ctas(int ep) {
+  return ep == kEps<MODE>[0]   ? per_sm_ctas_ep<MODE, kEps<MODE>[0]>()
+         : ep == kEps<MODE>[1] ? per_sm_ctas_ep<MODE, kEps<MODE>[1]>()
+                               : per_sm_ctas_ep<MODE, kEps<MODE>[2]>();
 }
 
 }  // namespace
@@ -323,7 +245,7 @@ struct heat_batch {
   int T = 0;
   int arith = HEAT_ARITH_EXACT;  // binary64 reading (the batch API is exact; the persistent form passes its own)
   int ctas_per_sm = 0;  // 0: as many as fit
-  int64_t seg_points = 16384;
+  int64_t window = 0;  // warp window in points (32 x points per lane); 0: the dtype's widest
   int64_t last_point_steps = 0;
   long long wait_ns = 5000000000LL;
   int32_t inj_ring_id = -1;  // test hook (heat_batch_inject_stall)
@@ -383,6 +305,18 @@ void arena_free(heat_batch *b, int64_t off, int64_t len) {
 
 int default_T(const heat_batch *b) { return b->dtype == HEAT_F32C ? 32 : 8; }
 
+// Widest warp window of the batch kernel for the dtype (points).
+int64_t widest_window(heat_dtype dtype) { return dtype == HEAT_F32C ? 1024 : 512; }
+
+// The batch's warp window for depth T: its setting (default the widest),
+// widened while a tile would hold fewer than 2T output points; 0 if even the
+// widest cannot.
+int64_t batch_window(const heat_batch *b, int T) {
+  int64_t w = b->window > 0 ? b->window : widest_window(b->dtype);
+  while (w - 2 * (int64_t)T < 2 * (int64_t)T && w < widest_window(b->dtype)) w *= 2;
+  return w - 2 * (int64_t)T >= 2 * (int64_t)T ? w : 0;
+}
+
 // Tiles of a ring's units computed on the integer pipes (binary64, exact
 // reading): the library's share for the ring's r unless
 // heat_batch_set_emulation chose one.
@@ -397,13 +331,16 @@ struct Table {
   std::vector<int64_t> segp, levp;
   std::vector<int32_t> active;
   int L = 0;
+  int64_t window = 0;  // warp window (points) the tiles were cut for
   int64_t point_steps = 0;
 };
 
 // Work table for advancing each live ring by steps_of(ring) (> 0) steps.
 template <typename F>
-Table build_table(const heat_batch *b, int T, int64_t seg_points, F steps_of) {
+Table build_table(const heat_batch *b, int T, int64_t window, F steps_of) {
+  const int64_t W = window - 2 * (int64_t)T;  // output points per warp tile
   Table t;
+  t.window = window;
   std::vector<std::pair<int64_t, int32_t>> order;  // (levels, id)
   for (int32_t id = 0; id < (int32_t)b->rings.size(); ++id) {
     const auto &r = b->rings[id];
@@ -423,7 +360,7 @@ Table build_table(const heat_batch *b, int T, int64_t seg_points, F steps_of) {
     d.off = r.off;
     d.n = r.n;
     d.steps = steps_of(r);
-    d.nseg = std::max<int64_t>(1, r.n / seg_points);
+    d.nseg = (r.n + W - 1) / W;
     d.done_base = t.segp.back();
     d.r = r.r;
     d.rf = r.rf;
@@ -524,11 +461,12 @@ int launch_table(heat_batch *b, const Table &t, int T) {
   const int64_t units = t.levp.back();
   const bool f32 = b->dtype == HEAT_F32C;
   const bool fma = !f32 && b->arith == HEAT_ARITH_FMA;
-  int per_sm = f32 ? heat::per_sm_ctas<2>() : fma ? heat::per_sm_ctas<1>() : heat::per_sm_ctas<0>();
+  const int ep = (int)(t.window / 32);
+  int per_sm = f32 ? heat::per_sm_ctas<2>(ep) : fma ? heat::per_sm_ctas<1>(ep) : heat::per_sm_ctas<0>(ep);
   if (per_sm < 1) return HEAT_ECUDA;
   if (b->ctas_per_sm > 0 && b->ctas_per_sm < per_sm) per_sm = b->ctas_per_sm;
   const int resident = per_sm * b->sms;
-  const int grid = (int)std::min<int64_t>(resident, units);
+  const int grid = (int)std::min<int64_t>(resident, (units + heat::kBWarps - 1) / heat::kBWarps);
   // The run is four stream operations: the table upload (from the pinned
   // staging buffer), two counter resets and the launch.  They are captured
   // into a CUDA graph and replayed while their shape -- byte counts, grid,
@@ -545,8 +483,8 @@ int launch_table(heat_batch *b, const Table &t, int T) {
     if (e == cudaSuccess) e = cudaMemsetAsync(b->d_done, 0, ndone * sizeof(unsigned), b->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->d_counter, 0, sizeof(unsigned long long), b->stream);
     if (e == cudaSuccess)
-      e = f32 ? heat::launch_batch<2>(a, grid, b->stream)
-              : fma ? heat::launch_batch<1>(a, grid, b->stream) : heat::launch_batch<0>(a, grid, b->stream);
+      e = f32 ? heat::launch_batch<2>(a, ep, grid, b->stream)
+              : fma ? heat::launch_batch<1>(a, ep, grid, b->stream) : heat::launch_batch<0>(a, ep, grid, b->stream);
     return e;
   };
   // the run's shape: operation sizes, grid, kernel, stream, staging buffer and
@@ -556,7 +494,7 @@ int launch_table(heat_batch *b, const Table &t, int T) {
   key.shape[0] = bytes;
   key.shape[1] = ndone;
   key.shape[2] = (unsigned long long)grid;
-  key.shape[3] = (unsigned long long)(f32 ? 2 : fma ? 1 : 0);
+  key.shape[3] = (unsigned long long)((f32 ? 2 : fma ? 1 : 0) * 256 + ep);
   key.shape[4] = (unsigned long long)(uintptr_t)b->stream;
   key.shape[5] = (unsigned long long)(uintptr_t)b->h_stage;
   memcpy(&key.args, &a, sizeof(a));
@@ -733,7 +671,9 @@ int heat_batch_run(heat_batch *b, int64_t max_steps) {
   if (!b) return HEAT_EINVAL;
   if (b->host_error != HEAT_OK) return HEAT_ESTATE;
   const int T = b->T > 0 ? b->T : default_T(b);
-  Table t = build_table(b, T, b->seg_points, [&](const heat_batch::Ring &r) {
+  const int64_t window = batch_window(b, T);
+  if (window == 0) return HEAT_EINVAL;
+  Table t = build_table(b, T, window, [&](const heat_batch::Ring &r) {
     const int64_t left = r.nt - r.done;
     return max_steps > 0 ? std::min(left, max_steps) : left;
   });
@@ -813,12 +753,16 @@ int heat_batch_remove(heat_batch *b, int32_t ring_id) {
   return HEAT_OK;
 }
 
-int heat_batch_set_tuning(heat_batch *b, int T, int64_t seg_points) {
-  if (!b || T < 0 || T > heat::kMaxT || seg_points < 0 || (seg_points > 0 && seg_points < 512)) return HEAT_EINVAL;
-  const int win = b->dtype == HEAT_F32C ? 32 * heat::tb::TBC<2>::E : 32 * heat::tb::TBC<0>::E;
-  if (T > 0 && 2 * T >= win) return HEAT_EINVAL;
+int heat_batch_set_tuning(heat_batch *b, int T, int64_t window_points) {
+  if (!b || T < 0 || T > heat::kMaxT || window_points < 0) return HEAT_EINVAL;
+  if (window_points > 0) {
+    // the widest window of the kernel's three not above the request, at least the narrowest
+    const int64_t widest = widest_window(b->dtype);
+    int64_t w = widest / 4;
+    while (w * 2 <= window_points && w < widest) w *= 2;
+    b->window = w;
+  }
   if (T > 0) b->T = T;
-  if (seg_points > 0) b->seg_points = seg_points;
   return HEAT_OK;
 }
 
@@ -957,7 +901,7 @@ int heat_batch_autotune(heat_batch *b, int *T_out, int64_t *seg_out) {
         if (strcmp(k2, key) == 0 && sscanf(bar + 1, "%d %lld", &T, &sg) == 2) {
           fclose(f);
           b->T = T;
-          b->seg_points = sg;
+          b->window = sg;
           if (T_out) *T_out = T;
           if (seg_out) *seg_out = sg;
           return HEAT_OK;
@@ -966,19 +910,21 @@ int heat_batch_autotune(heat_batch *b, int *T_out, int64_t *seg_out) {
       fclose(f);
     }
   }
-  const int Ts64[] = {2, 4, 8, 16};
+  const int Ts64[] = {4, 8, 12, 16};
   const int Ts32[] = {16, 32, 64};
-  const int64_t segs[] = {4096, 16384, 65536};
   const int *Ts = b->dtype == HEAT_F32C ? Ts32 : Ts64;
   const int nT = b->dtype == HEAT_F32C ? 3 : 4;
+  const int64_t widest = widest_window(b->dtype);
+  const int64_t wins[] = {widest / 4, widest / 2, widest};
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return HEAT_ECUDA;
   double best = -1;
   int bestT = b->T;
-  int64_t bestSeg = b->seg_points;
+  int64_t bestSeg = b->window;
   for (int ti = 0; ti < nT && rc == HEAT_OK; ++ti) {
-    for (int64_t sg : segs) {
+    for (int64_t sg : wins) {
       const int T = Ts[ti];
+      if (sg - 2 * T < 2 * T) continue;  // a tile must keep 2T output points
       // one level per ring: reads each ring's current buffer, writes only the idle one
       Table t = build_table(b, T, sg, [&](const heat_batch::Ring &r) { return std::min<int64_t>(r.nt - r.done, T); });
       for (int rep = 0; rep < 2 && rc == HEAT_OK; ++rep) {
@@ -1003,7 +949,7 @@ int heat_batch_autotune(heat_batch *b, int *T_out, int64_t *seg_out) {
   if (rc == HEAT_OK) rc = batch_sync_status(b);
   if (rc != HEAT_OK) return rc;
   b->T = bestT;
-  b->seg_points = bestSeg;
+  b->window = bestSeg;
   if (cache) {
     FILE *f = fopen(cache, "a");
     if (f) {
@@ -1020,83 +966,8 @@ int heat_batch_autotune(heat_batch *b, int *T_out, int64_t *seg_out) {
 
 namespace heat {
 
-// HEAT_FORM_PERSIST_TB for a single ring: one launch advances all nt steps.
-// Rings of at least three warp windows take the warp-granular dependency
-// kernel (k_wave.cu); shorter rings the work-table kernel over one ring whose
-// two buffers are the context's own, segments sized so that the levels keep
-// every CTA busy.
-int run_persist_tb(heat_ctx *c, int64_t nt) {
-  {
-    const int T = c->T > 0 ? c->T : (c->dtype == HEAT_F32C ? 32 : 12);
-    const int rc = run_wave(c, nt, T);
-    if (rc != HEAT_ENOTSUP) return rc;
-  }
-  if (!c->ptb) {
-    heat_batch *b = new (std::nothrow) heat_batch();
-    if (!b) return HEAT_ENOMEM;
-    b->dtype = c->dtype;
-    b->elem = c->elem;
-    b->device = c->device;
-    b->sms = c->sms;
-    b->dstat = c->dstat;  // shared with the context: its errors surface at heat_sync
-    if (cudaEventCreateWithFlags(&b->staged, cudaEventDisableTiming) != cudaSuccess ||
-        cudaMalloc((void **)&b->d_counter, sizeof(unsigned long long)) != cudaSuccess) {
-      if (b->staged) cudaEventDestroy(b->staged);
-      delete b;
-      return HEAT_ENOMEM;
-    }
-    c->ptb = b;
-  }
-  heat_batch *b = c->ptb;
-  b->stream = c->stream;
-  b->arith = c->arith;
-  b->arena[0] = c->buf[0];
-  b->arena[1] = c->buf[1];
-  b->wait_ns = c->wait_ns;
-  b->emul_share = c->emul_auto ? -1 : c->emul_share;  // heat_set_emulation applies here too
-  // default depth: 32 for binary32; 12 for binary64, the depth at which the
-  // integer tiles' screen still admits ordinary data for a general r
-  const int T = c->T > 0 ? c->T : (c->dtype == HEAT_F32C ? 32 : 12);
-  const int win = c->dtype == HEAT_F32C ? 32 * tb::TBC<2>::E : 32 * tb::TBC<0>::E;
-  if (2 * T >= win) return HEAT_EINVAL;
-  heat_batch::Ring r;
-  r.live = true;
-  r.off = 0;
-  r.n = c->geo.N;
-  r.len = c->geo.N;
-  r.r = c->r;
-  r.rf = c->rf;
-  r.nt = nt;
-  r.parity = c->cur;
-  b->rings.assign(1, r);
-  // about three segments per resident CTA, each at least 512 points
-  const int64_t per_sm = c->dtype == HEAT_F32C ? 3 : 5;
-  int64_t seg = c->geo.N / (3 * per_sm * c->sms);
-  if (seg < 512) seg = 512;
-  Table t = build_table(b, T, seg, [&](const heat_batch::Ring &rr) { return rr.nt; });
-  const int rc = launch_table(b, t, T);
-  if (rc != HEAT_OK) return rc;
-  const int64_t levels = (nt + T - 1) / T;
-  if (levels & 1) c->cur ^= 1;
-  c->steps += nt;
-  c->last_T = T;
-  c->last_launches = 1;
-  c->last_segments = (int)t.rings[0].nseg;
-  return HEAT_OK;
-}
-
-void free_persist_tb(heat_ctx *c) {
-  heat_batch *b = c->ptb;
-  if (!b) return;
-  if (b->stream) cudaStreamSynchronize(b->stream);
-  if (b->d_blob) cudaFree(b->d_blob);
-  if (b->d_done) cudaFree(b->d_done);
-  if (b->d_counter) cudaFree(b->d_counter);
-  if (b->h_stage) cudaFreeHost(b->h_stage);
-  if (b->staged) cudaEventDestroy(b->staged);
-  if (b->graph_exec) cudaGraphExecDestroy(b->graph_exec);
-  delete b;
-  c->ptb = nullptr;
-}
+// HEAT_FORM_PERSIST_TB for a single ring: one launch advances all nt steps
+// (k_wave.cu).
+int run_persist_tb(heat_ctx *c, int64_t nt) { return run_wave(c, nt, c->T > 0 ? c->T : wave_default_T(c)); }
 
 }  // namespace heat

@@ -86,6 +86,7 @@ _PROTOS = {
     "heat_batch_restore": (_int, [_vp]),
     "heat_batch_info": (_int, [_vp, ctypes.POINTER(_i32), ctypes.POINTER(_i64), ctypes.POINTER(_i64)]),
     "heat_run_noalloc": (_int, [_vp, _vp, _i64, _d, _d, _d, _i64, _int, _vp]),
+    "heat_probe_pipes": (_int, [_vp, ctypes.POINTER(_d), ctypes.POINTER(_d), ctypes.POINTER(_d)]),
     "heat_strerror": (ctypes.c_char_p, [_int]),
 }
 
@@ -261,6 +262,14 @@ def heat_run_noalloc(dev_u0, dev_u, n: int, k: float, dt: float, dx: float, nt: 
                                   int(nt), int(arith), handle), "heat_run_noalloc")
 
 
+def heat_probe_pipes(stream=None) -> dict:
+    """Measured lane operations per second: binary64 FMA, binary64 add, integer ALU."""
+    handle = None if stream is None else int(getattr(stream, "cuda_stream", stream))
+    f, a, i = _d(), _d(), _d()
+    _check(lib().heat_probe_pipes(handle, ctypes.byref(f), ctypes.byref(a), ctypes.byref(i)), "heat_probe_pipes")
+    return {"dfma_lane_ops_per_s": f.value, "dadd_lane_ops_per_s": a.value, "alu_lane_ops_per_s": i.value}
+
+
 def heat_batch_create(capacity_points: int, dtype: int = HEAT_F64) -> int:
     h = _vp()
     _check(lib().heat_batch_create(ctypes.byref(h), int(capacity_points), int(dtype)), "heat_batch_create")
@@ -317,8 +326,8 @@ def heat_batch_remove(b: int, ring: int) -> None:
     _check(lib().heat_batch_remove(b, int(ring)), "heat_batch_remove")
 
 
-def heat_batch_set_tuning(b: int, T: int = 0, seg_points: int = 0) -> None:
-    _check(lib().heat_batch_set_tuning(b, int(T), int(seg_points)), "heat_batch_set_tuning")
+def heat_batch_set_tuning(b: int, T: int = 0, window_points: int = 0) -> None:
+    _check(lib().heat_batch_set_tuning(b, int(T), int(window_points)), "heat_batch_set_tuning")
 
 
 def heat_batch_autotune(b: int) -> tuple[int, int]:

@@ -37,3 +37,13 @@ def test_reference_config_matches_the_gpu_arm_keys():
 
 def test_other_ranks_stay_silent():
     assert run("--workload", "ring-4000-f64", "--steps", "1", env={"RANK": "1", "WORLD_SIZE": "2"}) == []
+
+
+def test_cpu_report_runs_the_paper_shaped_configurations_in_full():
+    p = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--cpu-report"], capture_output=True,
+                       text=True, cwd=ROOT, timeout=300)
+    assert p.returncode == 0, p.stderr[-2000:]
+    (d,) = [json.loads(l)["cpu_report"] for l in p.stdout.splitlines() if l.startswith("{")]
+    assert d["C0_oracle"]["N"] == 10**6 and d["C0_oracle"]["nt"] == 1000 and d["C0_oracle"]["glups"] > 0
+    assert d["C1_oracle"]["N"] == 4000 and d["C1_oracle"]["nt"] == 100
+    assert {r["threads"] for r in d["C0_threaded"]} >= {2, 20, 40}

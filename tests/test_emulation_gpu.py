@@ -130,16 +130,31 @@ def test_power_of_two_r_fp64_tiles(r, share):
 
 @pytest.mark.parametrize("k", [0.3, 0.25])
 def test_two_engine_split_on_a_large_ring_is_bitwise_the_oracle(k):
-    """The library's default on 2^22 points (adaptive split between the FP64
-    unit and the integer pipes, depth 12, three blocks and a partial one),
-    element by element against the oracle."""
+    """The temporal-blocking form's default on 2^22 points (adaptive split
+    between the FP64 unit and the integer pipes, depth 12, three blocks and a
+    partial one), element by element against the oracle."""
     n = 1 << 22
     u0 = workloads.uniform_plus_mode(n, seed=11, m=5)
-    with H.Heat(n // 8, 8, k, 1.0, 1.0) as h:
+    with H.Heat(n // 8, 8, k, 1.0, 1.0, form="tblock") as h:
         got = h.set(u0).run(40).get()
         assert H.heat_get_emulation(h.ctx) == -1
         assert H.heat_last_run(h.ctx)["T"] == 12
     assert np.array_equal(bits(got), bits(oracle.run(u0, k, 40)))
+
+
+@pytest.mark.parametrize("k", [0.25, 0.3])
+def test_library_default_on_mid_size_rings_is_bitwise_the_oracle(k):
+    """The library's default from 2^19 to 2^26 binary64 points: one
+    dependency-driven launch (persistent temporal blocking, warp tiles split
+    between the FP64 unit and the integer pipes), depth 8 below 2^21 points and
+    16 above, element by element against the oracle with a partial last block."""
+    for n, T in [(1 << 19, 8), (10**6, 8), (1 << 22, 16)]:
+        u0 = workloads.uniform_plus_mode(n, seed=12, m=5)
+        with H.Heat(n // 4, 4, k, 1.0, 1.0) as h:
+            got = h.set(u0).run(3 * T + 5).get()
+            last = H.heat_last_run(h.ctx)
+        assert (last["form"], last["T"], last["launches"]) == ("persist_tb", T, 1), n
+        assert np.array_equal(bits(got), bits(oracle.run(u0, k, 3 * T + 5))), n
 
 
 @pytest.mark.parametrize("T", [0, 8])
@@ -147,13 +162,13 @@ def test_two_engine_split_on_a_large_ring_is_bitwise_the_oracle(k):
 @pytest.mark.parametrize("r", [0.25, 0.3])
 def test_persistent_temporal_blocking_takes_the_share(share, r, T):
     """heat_set_emulation reaches the persistent temporal-blocking form (one
-    batch launch for the ring); every share gives the oracle's bits, at the
-    default depth (12) and at 8."""
+    launch for the ring); every share gives the oracle's bits, at the default
+    depth and at 8."""
     n = 5 * 4096 + 77
     u0 = workloads.uniform(n, 40 + share, -1, 1)
     u0[300:340] = 0.0
     with H.Heat(n, 1, r, 1.0, 1.0, form="persist_tb", T=T) as h:
         H.heat_set_emulation(h.ctx, share)
         got = h.set(u0).run(37).get()
-        assert H.heat_last_run(h.ctx)["T"] == (T or 12)
+        assert H.heat_last_run(h.ctx)["T"] == (T or 8)
     assert np.array_equal(bits(got), bits(oracle.run(u0, r, 37)))

@@ -1,4 +1,4 @@
-"""Persistent flag-queue form: segmentation choices, and the bounded waits.
+"""Persistent forms: segmentation choices, and the bounded waits.
 
 The fault is made on the host side: a test hook tells one segment's CTA to stop
 publishing its edge values, so its neighbours' bounded waits run out, the run
@@ -84,3 +84,30 @@ def test_device_stays_usable_after_timeout():
     import torch
     x = torch.arange(10, device="cuda", dtype=torch.float64)
     assert float(x.sum().item()) == 45.0
+
+
+@pytest.mark.parametrize("tile,step", [(0, 0), (5, 16), (40, 33)])
+def test_stalled_tile_times_out_cleanly_in_persistent_temporal_blocking(tile, step):
+    """HEAT_FORM_PERSIST_TB: a tile that stops publishing its completion makes its
+    neighbours' bounded waits run out; the run reports HEAT_ETIMEOUT, every
+    warp returns, and the context works again after heat_set."""
+    n = 1 << 16
+    u0 = workloads.uniform(n, 4, -1, 1)
+    with H.Heat(n, 1, 0.25, 1.0, 1.0, form="persist_tb", T=8) as h:
+        H.heat_set_wait_limit(h.ctx, 50_000_000)       # 50 ms
+        H.heat_inject_stall(h.ctx, tile, step)
+        h.set(u0)
+        t0 = time.time()
+        h.run(64)
+        with pytest.raises(H.HeatError) as e:
+            h.sync()
+        assert e.value.code == H.HEAT_ETIMEOUT
+        assert time.time() - t0 < 10.0
+        assert H.heat_last_run(h.ctx)["segments"] > tile
+        with pytest.raises(H.HeatError) as e:
+            h.run(1)
+        assert e.value.code == H.HEAT_ESTATE
+        H.heat_inject_stall(h.ctx, -1, 0)
+        h.set(u0).run(64)
+        got = h.get()
+    assert np.array_equal(bits(got), bits(oracle.run(u0, 0.25, 64)))
