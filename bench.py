@@ -553,6 +553,8 @@ class RingRunner:
             srcs.append("paper_2307_01117_gb300/csrc/tb_core.cuh")
         if name in ("k_tblock", "k_wave"):
             srcs.append("paper_2307_01117_gb300/csrc/dp_emul.cuh")
+        if name == "k_wave":
+            srcs.append("paper_2307_01117_gb300/csrc/wave_core.cuh")
         steps_per_launch = self.nt / launches
         elem = 8.0 if self.w["dtype"] == "f64" else 4.0
         # every point read once and written once per launch; the persistent form
@@ -682,7 +684,9 @@ class BatchRunner:
         level_points = sum(-(-s.nt // T) * s.n for s in self.specs)
         return {"kernel": "k_batch", "src": ["paper_2307_01117_gb300/csrc/k_batch.cu",
                                              "paper_2307_01117_gb300/csrc/tb_core.cuh",
-                                             "paper_2307_01117_gb300/csrc/dp_emul.cuh"],
+                                             "paper_2307_01117_gb300/csrc/dp_emul.cuh",
+                                             "paper_2307_01117_gb300/csrc/wave_core.cuh",
+                                             "paper_2307_01117_gb300/csrc/stencil_ops.cuh"],
                 "launches": 1, "launch_ms": statistics.mean(run_ms), "point_steps_per_launch": self.point_steps,
                 "alg_bytes_per_launch": 2.0 * elem * level_points, "form": "batch", "T": T,
                 "segments": self.tuned[1],

@@ -80,7 +80,7 @@ typedef enum {
   HEAT_FORM_AUTO = 3,    /* library picks (measured fastest for each range):
                             HEAT_FORM_CLUSTER for every ring the cluster form
                             takes, HEAT_FORM_PERSIST_TB for binary64 rings under
-                            the exact reading from 2^19 to 2^26 points,
+                            the exact reading from 2^18 to 2^26 points,
                             HEAT_FORM_TBLOCK otherwise */
   HEAT_FORM_CLUSTER = 4, /* small rings (up to 16 x 4 windows of output, about
                             31000 binary64 points at T = 8): one thread-block
@@ -161,11 +161,11 @@ int heat_set_stream(heat_ctx *c, void *cuda_stream);
  * that is not a power of two), else 12 when part of the tiles run on the
  * integer pipes, else 8 below 2^22 points and 4 from 2^22 points; in the
  * cluster form 16, or 8 for rings that one cluster holds only at that depth;
- * in the persistent temporal-blocking form 32 for HEAT_F32C, for HEAT_F64 8
- * below 2^21 points and 16 from 2^21).  T is ignored by the one-step forms.
+ * in the persistent temporal-blocking form 32 for HEAT_F32C, for HEAT_F64 16
+ * below 2^19 points, 8 from 2^19 to 2^21 and 16 from 2^21).  T is ignored by the one-step forms.
  * HEAT_FORM_AUTO (the default) is HEAT_FORM_CLUSTER for binary64 rings of at
  * most 6144 points and binary32 rings that one thread-block cluster holds,
- * HEAT_FORM_PERSIST_TB for binary64 rings under the exact reading from 2^19 to
+ * HEAT_FORM_PERSIST_TB for binary64 rings under the exact reading from 2^18 to
  * 2^26 points, else HEAT_FORM_TBLOCK. */
 int heat_set_form(heat_ctx *c, int form, int T);
 

@@ -101,12 +101,16 @@ __global__ void __launch_bounds__(kBWarps * 32, MODE == 2 ? 1 : 8) k_batch(Batch
   const int wib = threadIdx.x >> 5;
   const int64_t total = a.levp[a.L];
   const bool int_warp = MODE == 0 && a.dual && (((blockIdx.x ^ wib) & 1) != 0);
+  // The next chunk is claimed before the current one is computed (its round
+  // trip overlaps the work); chunks still run in increasing order.
+  unsigned long long next = 0;
+  if (lane == 0) next = atomicAdd(a.counter, (unsigned long long)kChunk);
   for (;;) {
-    unsigned long long u0 = 0;
+    unsigned long long u0 = next;
     int go = 1;
     if (lane == 0) {
-      u0 = atomicAdd(a.counter, (unsigned long long)kChunk);
       go = (int64_t)u0 < total && !wave::aborted(a.st);
+      if (go) next = atomicAdd(a.counter, (unsigned long long)kChunk);
     }
     u0 = __shfl_sync(tb::kFull, u0, 0);
     if (!__shfl_sync(tb::kFull, go, 0)) break;
@@ -130,7 +134,6 @@ __global__ void __launch_bounds__(kBWarps * 32, MODE == 2 ? 1 : 8) k_batch(Batch
         stop = true;
         break;
       }
-      __syncwarp();
       int64_t lo, hi;
       wave::tile_bounds(R.n, nseg, j, lo, hi);
       const int par = R.parity ^ (int)(b & 1);

@@ -71,6 +71,10 @@ __global__ void __launch_bounds__(kWaveWarps * 32, MODE == 2 ? 1 : 8) k_wave(Wav
   const int wib = threadIdx.x >> 5;
   const int64_t nt_ = a.ntiles;
   const bool int_warp = MODE == 0 && a.dual && (((blockIdx.x ^ wib) & 1) != 0);
+  // One unit claimed at a time: a unit claimed ahead would wait behind its
+  // warp's current one, and on mid-size rings (a level not much larger than
+  // the resident warps) its neighbours at the next level would wait with it
+  // (10^6 points: 262 vs 281 GLUP/s).
   for (;;) {
     unsigned long long u = 0;
     int go = 1;
@@ -82,7 +86,6 @@ __global__ void __launch_bounds__(kWaveWarps * 32, MODE == 2 ? 1 : 8) k_wave(Wav
     if (!__shfl_sync(tb::kFull, go, 0)) break;
     const int64_t b = (int64_t)u / nt_, i = (int64_t)u - b * nt_;
     if (b > 0 && !wave::wait_neighbours(a.done, nt_, i, (unsigned)b, a.wait_ns, a.st, (int)i, lane)) break;
-    __syncwarp();
     int64_t lo, hi;
     wave::tile_bounds(a.N, nt_, i, lo, hi);
     const int par = (a.cur ^ (int)(b & 1)) & 1;
@@ -166,22 +169,26 @@ void free_wave(heat_ctx *c) {
   c->wave_cap = 0;
 }
 
-// Default depth: binary32 pairs 32 steps per pass; binary64 8 below 2^21
-// points (10^6 points, r = 1/4: 283.5 GLUP/s at 8, 279.2 at 10, 272.0 at 12,
-// 255.7 at 16), else 16 (2^22 points: 316.9 at 16, 305.3 at 12; deeper blocks
-// leave a general r's integer tiles without a screen that admits their data).
+// Default depth: binary32 pairs 32 steps per pass.  Binary64: 16 below 2^19
+// points, where the chain of levels (each waits on the one before) is the
+// bound and fewer levels pay more than the narrower tiles' halo costs (2^18
+// points: 171.8 GLUP/s at 16, 169.7 at 12, 159.9 at 8); 8 from 2^19 to 2^21,
+// where the halo of the narrowest window weighs most (10^6 points: 281.4 at 8,
+// 269.8 at 12, 253.3 at 16); 16 above (2^22 points: 317.0 at 16, 309.6 at 12).
 int wave_default_T(const heat_ctx *c) {
   if (c->dtype == HEAT_F32C) return 32;
+  if (c->geo.N < (1LL << 19)) return 16;
   return c->geo.N < (1LL << 21) ? 8 : 16;
 }
 
 // HEAT_FORM_AUTO takes this form for binary64 rings under the exact reading
-// from 2^19 to 2^26 points, where it measured faster than one launch per block
-// (10^6 points: 283.5 vs 236.3 GLUP/s at r = 1/4, 208.4 vs 191.0 at r = 0.3;
-// 2^24 points: 321.5 vs 311.2); on the 2^28-point ring the per-launch form
-// stays ahead (334.7 vs 323.6).
+// from 2^18 to 2^26 points, where it measured faster than one launch per block
+// (r = 1/4 / r = 0.3, GLUP/s: 2^18 points 171.8 vs 161.4 / 131.2 vs 119.3;
+// 10^6 points 281.4 vs 236.2 / 218.8 vs 190.7; 2^24 points 326.2 vs 309.8 /
+// 259.8 vs 241.9); from 2^26 points the per-launch form stays ahead (2^28:
+// 334.8 vs 327.9 / 263.8 vs 260.8).
 bool wave_preferred(const heat_ctx *c) {
-  return c->dtype == HEAT_F64 && c->arith == HEAT_ARITH_EXACT && c->geo.N >= (1LL << 19) && c->geo.N < (1LL << 26);
+  return c->dtype == HEAT_F64 && c->arith == HEAT_ARITH_EXACT && c->geo.N >= (1LL << 18) && c->geo.N < (1LL << 26);
 }
 
 // One launch for all nt steps.

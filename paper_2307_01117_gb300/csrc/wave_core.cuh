@@ -70,18 +70,20 @@ static __device__ __noinline__ bool wait_counter(const unsigned *p, unsigned tar
   return false;
 }
 
-// Lane 0 waits for tiles j-1, j, j+1 of a ring's counters to reach `level`;
-// the result is broadcast to the warp.
+// Wait until the counters of tiles j-1, j, j+1 of a ring reach `level`: lanes
+// 0, 1, 2 each acquire one counter (three loads in flight at once), and a
+// counter not yet there is waited for by its lane.  The warp barrier after the
+// vote orders every lane's later loads after the three acquires.
 __device__ __forceinline__ bool wait_neighbours(const unsigned *done, int64_t ntiles, int64_t j, unsigned level,
                                                 long long wait_ns, DevStatus *st, int where, int lane) {
-  int ok = 1;
-  if (lane == 0) {
-    const int64_t jm = j == 0 ? ntiles - 1 : j - 1, jp = j + 1 == ntiles ? 0 : j + 1;
-    ok = wait_counter(done + jm, level, wait_ns, st, where, level) &&
-         wait_counter(done + j, level, wait_ns, st, where, level) &&
-         wait_counter(done + jp, level, wait_ns, st, where, level);
+  bool ok = true;
+  if (lane < 3) {
+    const int64_t t = lane == 0 ? (j == 0 ? ntiles - 1 : j - 1) : lane == 1 ? j : (j + 1 == ntiles ? 0 : j + 1);
+    ok = ld_acquire_u32(done + t) >= level || wait_counter(done + t, level, wait_ns, st, where, level);
   }
-  return __shfl_sync(tb::kFull, ok, 0) != 0;
+  const bool all = __all_sync(tb::kFull, ok);
+  __syncwarp();
+  return all;
 }
 
 // Tile j of ntiles near-equal tiles of a ring of n points: the first
@@ -157,13 +159,12 @@ __device__ __forceinline__ void advance_tile(const typename tb::TBCx<MODE, EP>::
   }
 }
 
-// Publish a tile's completion: every lane's stores before lane 0's release.
+// Publish a tile's completion: the warp barrier orders every lane's stores
+// before lane 0's release, and the release makes them visible to whichever
+// warp acquires the counter.
 __device__ __forceinline__ void publish(unsigned *p, unsigned value, int lane) {
   __syncwarp();
-  if (lane == 0) {
-    __threadfence();
-    st_release_u32(p, value);
-  }
+  if (lane == 0) st_release_u32(p, value);
 }
 
 }  // namespace wave

@@ -59,17 +59,20 @@ def test_every_form_bitwise_at_dt_dx_not_one(form, T, k, dt, dx):
 
 @pytest.mark.parametrize("k,dt,dx", COEFS)
 def test_large_ring_default_path_at_dt_dx_not_one(k, dt, dx):
-    """2^18 + 192 points: the temporal-blocking default splits its tiles between
-    the FP64 unit and the integer pipes, whose multiply takes r's bits."""
+    """2^18 + 192 points: the library's default (persistent temporal blocking)
+    splits its warp tiles between the FP64 unit and the integer pipes, whose
+    multiply takes r's bits; the temporal-blocking form does the same."""
     n, np_ = (1 << 18) + 192, 4
     u0 = workloads.uniform_plus_mode(n, seed=3, m=3)
     r = oracle.coef(k, dt, dx)
-    with H.Heat(n // np_, np_, k, dt, dx) as h:
-        h.set(u0).run(40)
-        got = h.get()
-        info = H.heat_last_run(h.ctx)
-    assert info["form"] == "tblock"
-    assert same_bits(got, oracle.run(u0, r, 40)), (k, dt, dx)
+    ref = oracle.run(u0, r, 40)
+    for form, want in (("auto", "persist_tb"), ("tblock", "tblock")):
+        with H.Heat(n // np_, np_, k, dt, dx, form=form) as h:
+            h.set(u0).run(40)
+            got = h.get()
+            info = H.heat_last_run(h.ctx)
+        assert info["form"] == want
+        assert same_bits(got, ref), (form, k, dt, dx)
 
 
 @pytest.mark.parametrize("form,T", [("plain", 0), ("tblock", 8), ("auto", 0), ("persist_tb", 16)])

@@ -144,11 +144,12 @@ def test_two_engine_split_on_a_large_ring_is_bitwise_the_oracle(k):
 
 @pytest.mark.parametrize("k", [0.25, 0.3])
 def test_library_default_on_mid_size_rings_is_bitwise_the_oracle(k):
-    """The library's default from 2^19 to 2^26 binary64 points: one
+    """The library's default from 2^18 to 2^26 binary64 points: one
     dependency-driven launch (persistent temporal blocking, warp tiles split
-    between the FP64 unit and the integer pipes), depth 8 below 2^21 points and
-    16 above, element by element against the oracle with a partial last block."""
-    for n, T in [(1 << 19, 8), (10**6, 8), (1 << 22, 16)]:
+    between the FP64 unit and the integer pipes), depth 16 below 2^19 points, 8
+    from 2^19 to 2^21 and 16 above, element by element against the oracle with
+    a partial last block."""
+    for n, T in [(1 << 18, 16), (1 << 19, 8), (10**6, 8), (1 << 22, 16)]:
         u0 = workloads.uniform_plus_mode(n, seed=12, m=5)
         with H.Heat(n // 4, 4, k, 1.0, 1.0) as h:
             got = h.set(u0).run(3 * T + 5).get()
@@ -170,5 +171,5 @@ def test_persistent_temporal_blocking_takes_the_share(share, r, T):
     with H.Heat(n, 1, r, 1.0, 1.0, form="persist_tb", T=T) as h:
         H.heat_set_emulation(h.ctx, share)
         got = h.set(u0).run(37).get()
-        assert H.heat_last_run(h.ctx)["T"] == (T or 8)
+        assert H.heat_last_run(h.ctx)["T"] == (T or 16)   # the default below 2^19 points
     assert np.array_equal(bits(got), bits(oracle.run(u0, r, 37)))
