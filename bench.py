@@ -770,7 +770,10 @@ class ServeRunner:
 
     def _window(self, duration, seed):
         reqs = self.workloads.request_stream(rate=self.rate, duration=duration, seed=seed)
-        srv = self.serve.HeatServer(budget_bytes=self.w["budget"], tick_steps=self.args.tick, stream=self.stream)
+        if self.args.server == "kernel":
+            srv = self.serve.KernelServer(budget_bytes=self.w["budget"], stream=self.stream)
+        else:
+            srv = self.serve.HeatServer(budget_bytes=self.w["budget"], tick_steps=self.args.tick, stream=self.stream)
         try:
             return srv.serve(reqs, duration=duration)
         finally:
@@ -797,14 +800,17 @@ class ServeRunner:
         return 0, 0
 
     def kernel_info(self, run_ms):
+        # kernel server: `ticks` counts server-kernel launches (both dtypes);
+        # runs: one launch per arena and run
         ticks = max(1, sum(st.ticks for st in self.windows))
         ps = sum(st.gpu_point_steps for st in self.windows)
-        per_window = max(1, 2 * ticks // max(1, len(self.windows)))
-        return {"kernel": "k_batch", "src": ["paper_2307_01117_gb300/csrc/k_batch.cu",
-                                             "paper_2307_01117_gb300/csrc/tb_core.cuh",
-                                             "paper_2307_01117_gb300/csrc/dp_emul.cuh"],
+        per_window = max(1, ticks // max(1, len(self.windows)))
+        kernel, src = (("k_serve", "k_serve.cu") if self.args.server == "kernel" else ("k_batch", "k_batch.cu"))
+        return {"kernel": kernel, "src": [f"paper_2307_01117_gb300/csrc/{src}",
+                                          "paper_2307_01117_gb300/csrc/tb_core.cuh",
+                                          "paper_2307_01117_gb300/csrc/dp_emul.cuh"],
                 "launches": per_window, "launch_ms": statistics.mean(run_ms) / per_window,
-                "point_steps_per_launch": ps / (2 * ticks), "alg_bytes_per_launch": 0.0, "form": "serve",
+                "point_steps_per_launch": ps / ticks, "alg_bytes_per_launch": 0.0, "form": "serve",
                 "T": None, "segments": None}
 
     def latency(self):
@@ -821,7 +827,8 @@ class ServeRunner:
 
     def config(self):
         return {"workload": self.args.workload, "rate_req_s": self.rate, "window_s": self.duration,
-                "budget_bytes": self.w["budget"], "tick_steps": self.args.tick,
+                "budget_bytes": self.w["budget"], "server": self.args.server,
+                "tick_steps": self.args.tick if self.args.server == "runs" else None,
                 "requests": "N log-uniform [1e4, 1e7], nt uniform [100, 2000], r uniform [0.05, 0.5], "
                             "binary64 / binary32-compensated 50/50, u0 = U[-1,1) generated on the device",
                 "l2": "inputs larger than L2 (no flush needed)"}
@@ -873,19 +880,21 @@ def plain_subrecord(args, w, H, torch, local, stream, sms: int, pk: dict, probe:
             "headline_over_plain": None}
 
 
-def serving_subrecord(stream, rate: float = 100.0, duration: float = 10.0, tick: int = 256,
+def serving_subrecord(stream, server: str, rate: float = 100.0, duration: float = 10.0, tick: int = 256,
                       budget: float = 120e9) -> dict:
     """A short serving window (Poisson arrivals replayed in real time through the
     continuous-batching server, not drained): p50/p99 latency, GLUP/s, backlog."""
     from paper_2307_01117_gb300 import serve, workloads
-    srv = serve.HeatServer(budget_bytes=budget, tick_steps=tick, stream=stream)
+    srv = (serve.KernelServer(budget_bytes=budget, stream=stream) if server == "kernel"
+           else serve.HeatServer(budget_bytes=budget, tick_steps=tick, stream=stream))
     try:
         srv.serve(workloads.request_stream(rate=rate, duration=2.0, seed=1002), duration=2.0)   # warm-up
         st = srv.serve(workloads.request_stream(rate=rate, duration=duration, seed=2), duration=duration)
     finally:
         srv.close()
     s = st.summary()
-    return {"rate_req_s": rate, "window_s": duration, "tick_steps": tick, "budget_bytes": budget,
+    return {"rate_req_s": rate, "window_s": duration, "server": server,
+            "tick_steps": tick if server == "runs" else None, "budget_bytes": budget,
             "p50_s": s["p50_s"], "p99_s": s["p99_s"], "submitted": s["submitted"], "completed": s["completed"],
             "backlog_at_window_end": s["backlog"], "completed_glups": s["completed_glups"],
             "advanced_glups": s["advanced_glups"], "max_inflight": s["max_inflight"],
@@ -914,7 +923,9 @@ def main() -> int:
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--rate", type=float, default=0.0, help="serving workloads: arrivals per second")
     ap.add_argument("--duration", type=float, default=0.0, help="serving workloads: window length (s)")
-    ap.add_argument("--tick", type=int, default=256, help="serving workloads: steps per tick")
+    ap.add_argument("--tick", type=int, default=256, help="serving workloads: steps per run (--server runs)")
+    ap.add_argument("--server", default="kernel", choices=["kernel", "runs"],
+                    help="serving: requests join one running kernel (kernel) or queued batch runs (runs)")
     ap.add_argument("--cpu-report", action="store_true",
                     help="print the CPU baselines on the paper-shaped configurations (no GPU) and exit")
     ap.add_argument("--no-plain", action="store_true", help="leave out the plain-form sub-record")
@@ -1072,7 +1083,7 @@ def main() -> int:
         plain = plain_subrecord(args, w, H, torch, local, stream, sms, pk, probe)
         plain["headline_over_plain"] = value / plain["value"]
     if args.workload == DEFAULT_WORKLOAD and not args.no_serving:
-        serving = serving_subrecord(stream)
+        serving = serving_subrecord(stream, args.server)
 
     cb = ct = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and w["kind"] != "serve":

@@ -392,6 +392,78 @@ int heat_batch_restore(heat_batch *b);
 int heat_batch_info(const heat_batch *b, int32_t *live_rings, int64_t *largest_free_points,
                     int64_t *last_point_steps);
 
+/* ---------------------------------------------------------------------------
+ * Request server: continuous batching inside one running kernel.  Requests
+ * (independent instances of Section 2's problem, each its own size, coefficient
+ * and step count) are admitted into a device arena and a slot table while a
+ * persistent kernel runs; its warps find admitted requests in the slot table,
+ * claim their (level, warp tile) units in level order from each request's own
+ * counter, wait (bounded) on the neighbouring tiles' completion counters as in
+ * the batched-ring kernel, and mark a request complete in host-mapped memory
+ * when its last unit is done.  A request submitted while others run joins the
+ * running kernel at once: no launch boundary, no host tick.  A request's result
+ * is bitwise the one heat_run gives for it alone (binary64) or the one the
+ * temporal-blocking form gives with the server's block depth (HEAT_F32C).
+ * The server kernel ends by itself after `idle_ns` without any admitted work;
+ * heat_server_submit starts it again.  While it runs, a device-wide
+ * synchronisation (cudaDeviceSynchronize) waits for it to end: synchronise
+ * streams instead.  The paper has no serving layer; this is the library's (it
+ * serves the paper's problem).
+ * ------------------------------------------------------------------------- */
+typedef struct heat_server heat_server; /* opaque, library-owned */
+
+/* Server for requests of dtype with room for `capacity_points` ring points
+ * (two arena buffers, allocated now) and at most `max_requests` (1..65536)
+ * requests in flight; T (1..64, 0: 16 for binary64, 32 for HEAT_F32C) is its
+ * temporal block depth (warp windows of 512 points).  ctas_per_sm caps the
+ * server kernel's CTAs per SM (0: one fewer than fit; the cap is always below
+ * what fits, so that the small copy and publish kernels of admission run beside
+ * it), so that two servers (binary64 and binary32) can share every SM. */
+int heat_server_create(heat_server **out, int64_t capacity_points, heat_dtype dtype, int32_t max_requests, int T,
+                       int ctas_per_sm);
+
+/* Stop the server kernel (it finishes its current units), wait for it and free
+ * everything.  NULL is a no-op. */
+void heat_server_destroy(heat_server *s);
+
+/* Admit a ring of n points with coefficient r = k*dt/dx^2 that advances nt >= 1
+ * steps from the initial state dev_u (n binary64 values in device memory,
+ * 8-byte aligned).  The copy into the arena is queued on the server's copy
+ * stream, which does not wait for other streams: dev_u must hold its values
+ * when the call is made and stay unchanged until the request is reported
+ * complete.  The request is published to the running kernel behind the copy
+ * (and the kernel launched if it is not running).  *req_id receives the
+ * request's handle.  HEAT_ENOMEM when the arena or the slot table has no room
+ * (the caller may retry after releasing completed requests); HEAT_ESTATE after
+ * a device error. */
+int heat_server_submit(heat_server *s, int64_t n, double k, double dt, double dx, int64_t nt, const double *dev_u,
+                       int32_t *req_id);
+
+/* Requests completed since the last call, without waiting: up to `max` ids into
+ * done_ids, their number into *count.  HEAT_ETIMEOUT if a bounded wait of the
+ * server kernel ran out (the server then refuses submissions). */
+int heat_server_poll(heat_server *s, int32_t *done_ids, int32_t max, int32_t *count);
+
+/* Queue a copy of a completed request's final state (n binary64 values) into
+ * device memory on the server's copy stream; `cuda_event`, if not NULL, is a
+ * cudaEvent_t recorded behind the copy.  HEAT_ESTATE if the request is not
+ * complete. */
+int heat_server_get_device(heat_server *s, int32_t req_id, double *dev_u, int64_t n, void *cuda_event);
+
+/* Free a completed request's slot and arena space (after copies queued on the
+ * copy stream). */
+int heat_server_release(heat_server *s, int32_t req_id);
+
+/* Point-steps of the requests completed so far, requests in flight, whether
+ * the server kernel is running, and how many times it has been launched.  Any
+ * pointer may be NULL. */
+int heat_server_info(const heat_server *s, int64_t *point_steps, int32_t *in_flight, int *running,
+                     int64_t *launches);
+
+/* Upper bound, in nanoseconds, on a unit's wait for its neighbours (default
+ * 5e9) and on the kernel's idle time before it ends (default 2e8). */
+int heat_server_set_limits(heat_server *s, int64_t wait_ns, int64_t idle_ns);
+
 /* Allocation-free stepper for callers that cannot allocate device memory
  * (inside CUDA graph capture, in real-time loops that must stay off the
  * allocator, or under another framework's memory pool).  The paper has no

@@ -86,6 +86,15 @@ _PROTOS = {
     "heat_batch_restore": (_int, [_vp]),
     "heat_batch_info": (_int, [_vp, ctypes.POINTER(_i32), ctypes.POINTER(_i64), ctypes.POINTER(_i64)]),
     "heat_run_noalloc": (_int, [_vp, _vp, _i64, _d, _d, _d, _i64, _int, _vp]),
+    "heat_server_create": (_int, [ctypes.POINTER(_vp), _i64, _int, _i32, _int, _int]),
+    "heat_server_destroy": (None, [_vp]),
+    "heat_server_submit": (_int, [_vp, _i64, _d, _d, _d, _i64, _vp, ctypes.POINTER(_i32)]),
+    "heat_server_poll": (_int, [_vp, ctypes.POINTER(_i32), _i32, ctypes.POINTER(_i32)]),
+    "heat_server_get_device": (_int, [_vp, _i32, _vp, _i64, _vp]),
+    "heat_server_release": (_int, [_vp, _i32]),
+    "heat_server_info": (_int, [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i32), ctypes.POINTER(_int),
+                                ctypes.POINTER(_i64)]),
+    "heat_server_set_limits": (_int, [_vp, _i64, _i64]),
     "heat_probe_pipes": (_int, [_vp, ctypes.POINTER(_d), ctypes.POINTER(_d), ctypes.POINTER(_d)]),
     "heat_strerror": (ctypes.c_char_p, [_int]),
 }
@@ -268,6 +277,59 @@ def heat_probe_pipes(stream=None) -> dict:
     f, a, i = _d(), _d(), _d()
     _check(lib().heat_probe_pipes(handle, ctypes.byref(f), ctypes.byref(a), ctypes.byref(i)), "heat_probe_pipes")
     return {"dfma_lane_ops_per_s": f.value, "dadd_lane_ops_per_s": a.value, "alu_lane_ops_per_s": i.value}
+
+
+def heat_server_create(capacity_points: int, dtype: int = HEAT_F64, max_requests: int = 4096, T: int = 0,
+                       ctas_per_sm: int = 0) -> int:
+    h = _vp()
+    _check(lib().heat_server_create(ctypes.byref(h), int(capacity_points), int(dtype), int(max_requests), int(T),
+                                    int(ctas_per_sm)), "heat_server_create")
+    return h.value
+
+
+def heat_server_destroy(s: int) -> None:
+    lib().heat_server_destroy(s)
+
+
+def heat_server_submit(s: int, n: int, k: float, dt: float, dx: float, nt: int, dev_u) -> int:
+    rid = _i32()
+    _check(lib().heat_server_submit(s, int(n), float(k), float(dt), float(dx), int(nt), _dev_ptr(dev_u),
+                                    ctypes.byref(rid)), "heat_server_submit")
+    return rid.value
+
+
+_poll_buf = (_i32 * 65536)()
+_poll_lock = threading.Lock()
+
+
+def heat_server_poll(s: int, max_ids: int = 65536) -> list:
+    """Ids of the requests completed since the last poll (no waiting)."""
+    l, cnt = lib(), _i32()
+    with _poll_lock:
+        _check(l.heat_server_poll(s, _poll_buf, min(int(max_ids), 65536), ctypes.byref(cnt)), "heat_server_poll")
+        return [_poll_buf[i] for i in range(cnt.value)]
+
+
+def heat_server_get_device(s: int, req: int, dev_u, n: int, event=None) -> None:
+    """Queue the completed request's state into dev_u; `event` (a torch.cuda.Event
+    or a raw cudaEvent_t) is recorded behind the copy."""
+    ev = None if event is None else int(getattr(event, "cuda_event", event))
+    _check(lib().heat_server_get_device(s, int(req), _dev_ptr(dev_u), int(n), ev), "heat_server_get_device")
+
+
+def heat_server_release(s: int, req: int) -> None:
+    _check(lib().heat_server_release(s, int(req)), "heat_server_release")
+
+
+def heat_server_info(s: int) -> dict:
+    ps, fl, run, nl = _i64(), _i32(), _int(), _i64()
+    _check(lib().heat_server_info(s, ctypes.byref(ps), ctypes.byref(fl), ctypes.byref(run), ctypes.byref(nl)),
+           "heat_server_info")
+    return {"point_steps": ps.value, "in_flight": fl.value, "running": bool(run.value), "launches": nl.value}
+
+
+def heat_server_set_limits(s: int, wait_ns: int = 0, idle_ns: int = 0) -> None:
+    _check(lib().heat_server_set_limits(s, int(wait_ns), int(idle_ns)), "heat_server_set_limits")
 
 
 def heat_batch_create(capacity_points: int, dtype: int = HEAT_F64) -> int:

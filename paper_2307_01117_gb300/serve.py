@@ -244,6 +244,7 @@ class HeatServer:
         """Replay `requests` (arrival times in seconds from the start) in real time.
         Stops at `duration` (default: the last arrival) unless drain is set, in
         which case it runs until every admitted or queued request is done."""
+        self._finish_leftovers()
         stats = ServeStats()
         self._reset_queues()
         reqs = sorted(enumerate(requests), key=lambda x: x[1].t_arrive)
@@ -267,4 +268,194 @@ class HeatServer:
         stats.wall_s = time.perf_counter() - t0
         for b in self.batch.values():      # report a device error of the window, if any
             H.heat_batch_sync(b)
+        return stats
+
+    def _finish_leftovers(self) -> None:
+        """Run the requests a previous window left in flight to completion and
+        release their space, outside any window's clock and statistics."""
+        self.queue.clear()
+        scratch = ServeStats()
+        t0 = time.perf_counter()
+        while self.inflight or self.pending:
+            self.tick(t0, scratch)
+
+
+class KernelServer:
+    """Continuous batching inside one running kernel per dtype (heat_server_* in
+    include/heat.h): a request is admitted into its server's arena and slot
+    table and published to the running server kernel, whose warps take it up at
+    once -- no launch boundary, no host tick.  The host only admits, polls the
+    host-mapped completion words and moves finished states to pinned host
+    memory (device copy on the server's copy stream, then a host copy behind an
+    event), so latency runs from arrival to the result in host memory.
+
+    Admission is by free device memory under a byte budget (binary64 and
+    binary32 servers split it by the expected byte share of the request mix,
+    as HeatServer does), with a bounded lookahead past requests that do not fit
+    yet.  Each result is bitwise the request's solo result (binary64:
+    heat_run; binary32: the temporal-blocking form with the server's depth)."""
+
+    def __init__(self, budget_bytes: float, lookahead: int = 64, f32c_share: float = 1 / 3, T64: int = 0,
+                 T32: int = 16, stream=None, init_fn=None, ctas64: int = 4, ctas32: int = 2,
+                 max_requests: int = 4096):
+        import torch
+        self.torch = torch
+        self.lookahead = int(lookahead)
+        cap32 = max(1, int(budget_bytes * f32c_share) // 8)
+        cap64 = max(1, int(budget_bytes * (1 - f32c_share)) // 16)
+        self.caps = {False: cap64, True: cap32}
+        self.srv = {False: H.heat_server_create(cap64, H.HEAT_F64, max_requests, T64, ctas64)}
+        try:
+            self.srv[True] = H.heat_server_create(cap32, H.HEAT_F32C, max_requests, T32, ctas32)
+        except Exception:
+            H.heat_server_destroy(self.srv[False])
+            raise
+        self.stream = stream if stream is not None else torch.cuda.Stream()
+        self.init_fn = init_fn or self._device_uniform
+        self._reset_queues()
+
+    def _reset_queues(self) -> None:
+        self.queue: collections.deque = collections.deque()
+        self.inflight: dict = {}   # (f32c, request id) -> (index, request, t_admit, device input)
+        self.pending: list = []    # result copies in flight: (event, host array, index, request, t_admit)
+        self.results: dict = {}
+
+    def _device_uniform(self, req: Request):
+        torch = self.torch
+        g = torch.Generator(device="cuda")
+        g.manual_seed(req.seed)
+        return torch.empty(req.n, dtype=torch.float64, device="cuda").uniform_(-1.0, 1.0, generator=g)
+
+    def close(self):
+        for s in self.srv.values():
+            H.heat_server_destroy(s)
+        self.srv = {}
+
+    def submit(self, index: int, req: Request, stats: ServeStats) -> None:
+        stats.submitted += 1
+        if req.n + 64 > self.caps[req.f32c]:
+            stats.rejected_too_large += 1
+            return
+        self.queue.append((index, req))
+
+    # -- device specifics ---------------------------------------------------------------------
+
+    def _input(self, req: Request):
+        """The request's initial state on the device, complete (the server's copy
+        stream does not wait for other streams)."""
+        with self.torch.cuda.stream(self.stream):
+            u = self.init_fn(req)
+        self.stream.synchronize()
+        return u
+
+    def _fetch(self, f32: bool, rid: int, n: int):
+        """Queue a completed request's state to pinned host memory: the server's
+        device copy, then a host copy behind an event; returns (host array,
+        event, device buffer).  The device buffer is written on the server's copy
+        stream, which torch's allocator does not see: the caller keeps it until
+        the event has fired."""
+        torch = self.torch
+        s = self.srv[f32]
+        with torch.cuda.stream(self.stream):
+            dev = torch.empty(n, dtype=torch.float64, device="cuda")
+            landed = torch.cuda.Event()
+            landed.record(self.stream)      # creates the event; the server records it again behind its copy
+        H.heat_server_get_device(s, rid, dev, n, landed)
+        host = torch.empty(n, dtype=torch.float64, pin_memory=True)
+        with torch.cuda.stream(self.stream):
+            self.stream.wait_event(landed)
+            host.copy_(dev, non_blocking=True)
+            done = torch.cuda.Event()
+            done.record(self.stream)
+        return host.numpy(), done, dev
+
+    # ------------------------------------------------------------------------------------------
+
+    def _admit(self, now: float) -> None:
+        kept = collections.deque()
+        looked = 0
+        while self.queue and looked < self.lookahead:
+            index, req = self.queue.popleft()
+            looked += 1
+            u = self._input(req)
+            try:
+                rid = H.heat_server_submit(self.srv[req.f32c], req.n, req.r, 1.0, 1.0, req.nt, u)
+            except H.HeatError as e:
+                if e.code != H.HEAT_ENOMEM:
+                    raise
+                kept.append((index, req))   # no room yet: keep its place
+                continue
+            self.inflight[(req.f32c, rid)] = (index, req, now, u)
+        kept.extend(self.queue)
+        self.queue = kept
+
+    def _drain(self, f32: bool) -> None:
+        """Move the requests the server reports complete to pinned host memory."""
+        s = self.srv[f32]
+        for rid in H.heat_server_poll(s):
+            index, req, t_admit, _ = self.inflight.pop((f32, rid))
+            host, done, dev = self._fetch(f32, rid, req.n)
+            H.heat_server_release(s, rid)       # the space is reused behind the copy on the server's stream
+            self.pending.append((done, host, index, req, t_admit, dev))
+
+    def _finish_leftovers(self) -> None:
+        """Let the requests a previous window left in flight complete and release
+        them, outside any window's clock and statistics."""
+        self.queue.clear()
+        scratch = ServeStats()
+        t0 = time.perf_counter()
+        while self.inflight or self.pending:
+            for f32 in (False, True):
+                self._drain(f32)
+            self._collect(t0, scratch, False)
+            time.sleep(2e-4)
+
+    def _collect(self, t0: float, stats: ServeStats, keep_results: bool) -> None:
+        still = []
+        for item in self.pending:
+            ev, host, index, req, t_admit, _ = item
+            if ev.query():   # the device buffer goes back to the allocator only now
+                stats.done.append(Done(index, req.t_arrive, t_admit, time.perf_counter() - t0, req.n, req.nt,
+                                       req.f32c))
+                if keep_results:
+                    self.results[index] = host
+            else:
+                still.append(item)
+        self.pending = still
+
+    def serve(self, requests: list[Request], duration: float | None = None, drain: bool = False,
+              keep_results: bool = False) -> ServeStats:
+        """Replay `requests` (arrival times in seconds from the start) in real time;
+        the same contract as HeatServer.serve."""
+        self._finish_leftovers()
+        stats = ServeStats()
+        self._reset_queues()
+        reqs = sorted(enumerate(requests), key=lambda x: x[1].t_arrive)
+        horizon = duration if duration is not None else (reqs[-1][1].t_arrive if reqs else 0.0)
+        ps0 = sum(H.heat_server_info(s)["point_steps"] for s in self.srv.values())
+        launches0 = sum(H.heat_server_info(s)["launches"] for s in self.srv.values())
+        t0 = time.perf_counter()
+        nxt = 0
+        while True:
+            now = time.perf_counter() - t0
+            while nxt < len(reqs) and reqs[nxt][1].t_arrive <= now and reqs[nxt][1].t_arrive <= horizon:
+                self.submit(reqs[nxt][0], reqs[nxt][1], stats)
+                nxt += 1
+            arrivals_left = nxt < len(reqs) and reqs[nxt][1].t_arrive <= horizon
+            if now >= horizon and not drain:
+                break
+            if not self.queue and not self.inflight and not self.pending:
+                if not arrivals_left:
+                    break
+                time.sleep(max(0.0, min(0.01, reqs[nxt][1].t_arrive - now)))
+                continue
+            self._admit(now)
+            stats.max_inflight = max(stats.max_inflight, len(self.inflight))
+            for f32 in (False, True):
+                self._drain(f32)
+            self._collect(t0, stats, keep_results)
+            time.sleep(2e-4)
+        stats.wall_s = time.perf_counter() - t0
+        stats.gpu_point_steps = sum(H.heat_server_info(s)["point_steps"] for s in self.srv.values()) - ps0
+        stats.ticks = sum(H.heat_server_info(s)["launches"] for s in self.srv.values()) - launches0
         return stats

@@ -192,3 +192,103 @@ def test_runs_queue_ahead_and_results_count_when_their_copy_lands(monkeypatch):
     copies[0].ready = True
     srv.tick(0.0, st)
     assert [d.index for d in st.done] == [1]
+
+
+# --- the kernel server's host logic (KernelServer), against a fake heat_server_* ----------
+
+class FakeServers:
+    """Slots and arena occupancy only; a request completes after `polls_to_finish`
+    polls of its server (a stand-in for the running kernel)."""
+
+    def __init__(self, caps, slots=4, polls_to_finish=2):
+        self.caps, self.slots, self.polls_to_finish = caps, slots, polls_to_finish
+        self.live = {s: {} for s in caps}
+        self.submitted, self.released = [], []
+
+    def heat_server_submit(self, s, n, k, dt, dx, nt, u):
+        used = sum(r["n"] for r in self.live[s].values())
+        free = [i for i in range(self.slots) if i not in self.live[s]]
+        if not free or used + n > self.caps[s]:
+            raise FakeError(ENOMEM)
+        rid = free[0]
+        self.live[s][rid] = {"n": n, "polls": 0, "reported": False}
+        self.submitted.append((s, rid, n))
+        return rid
+
+    def heat_server_poll(self, s):
+        out = []
+        for rid, r in self.live[s].items():
+            r["polls"] += 1
+            if r["polls"] >= self.polls_to_finish and not r["reported"]:
+                r["reported"] = True
+                out.append(rid)
+        return out
+
+    def heat_server_release(self, s, rid):
+        assert self.live[s][rid]["reported"]
+        del self.live[s][rid]
+        self.released.append((s, rid))
+
+    def heat_server_info(self, s):
+        return {"point_steps": 0, "in_flight": len(self.live[s]), "running": True, "launches": 1}
+
+
+def make_kernel_server(monkeypatch, cap_points, slots=4, lookahead=64):
+    fake = FakeServers({"s64": cap_points, "s32": cap_points}, slots)
+    ns = types.SimpleNamespace(HeatError=FakeError, HEAT_ENOMEM=ENOMEM,
+                               **{k: getattr(fake, k) for k in dir(fake) if k.startswith("heat_server_")})
+    monkeypatch.setattr(serve, "H", ns)
+    srv = object.__new__(serve.KernelServer)
+    srv.lookahead = lookahead
+    srv.caps = {False: cap_points, True: cap_points}
+    srv.srv = {False: "s64", True: "s32"}
+    srv._input = lambda req: np.zeros(req.n)
+    srv._fetch = lambda f32, rid, n: (np.zeros(n), READY, None)
+    srv._reset_queues()
+    return srv, fake
+
+
+def test_kernel_server_admits_by_space_and_slots_and_releases_every_request(monkeypatch):
+    srv, fake = make_kernel_server(monkeypatch, cap_points=10_000, slots=2)
+    reqs = [req(0.0, 4000, 48) for _ in range(5)] + [req(0.0, 100, 48, f32c=True)]
+    st = srv.serve(reqs, drain=True)
+    assert len(st.done) == 6 and st.max_inflight >= 2
+    assert not srv.queue and not srv.inflight and not srv.pending
+    assert all(v == {} for v in fake.live.values())
+    assert sorted(fake.released) == sorted((s, rid) for s, rid, _ in fake.submitted)
+    order = [d.index for d in sorted((d for d in st.done if not d.f32c), key=lambda d: d.t_done)]
+    assert order[:2] == [0, 1] and sorted(order) == [0, 1, 2, 3, 4]   # waiting requests kept their places
+
+
+def test_kernel_server_lookahead_admits_a_small_request_behind_a_large_one(monkeypatch):
+    srv, fake = make_kernel_server(monkeypatch, cap_points=10_000, slots=8)
+    st = serve.ServeStats()
+    for i, r in enumerate([req(0.0, 6000, 32), req(0.0, 6000, 32), req(0.0, 1000, 32)]):
+        srv.submit(i, r, st)
+    srv._admit(0.0)
+    assert sorted(idx for idx, *_ in srv.inflight.values()) == [0, 2] and [i for i, _ in srv.queue] == [1]
+
+
+def test_kernel_server_rejects_oversized_requests(monkeypatch):
+    srv, fake = make_kernel_server(monkeypatch, cap_points=10_000)
+    st = srv.serve([req(0.0, 10_000, 16), req(0.0, 100, 16)], drain=True)
+    assert st.rejected_too_large == 1 and [d.index for d in st.done] == [1]
+
+
+def test_a_new_window_first_finishes_what_the_last_one_left_in_flight(monkeypatch):
+    srv, fake = make_server(monkeypatch, cap_points=100_000, tick_s=0.002)
+    st = srv.serve([req(0.0, 2000, 16 * 50)], duration=0.005)  # ends after a few runs, the request in flight
+    assert st.submitted == 1 and not st.done and srv.inflight
+    st2 = srv.serve([req(0.0, 1000, 16)], drain=True)
+    assert [d.index for d in st2.done] == [0] and all(r == {} for r in fake.rings.values())
+
+
+def test_kernel_server_window_finishes_the_last_windows_requests(monkeypatch):
+    srv, fake = make_kernel_server(monkeypatch, cap_points=10_000)
+    fake.polls_to_finish = 10**9                              # never completes within the first window
+    srv.serve([req(0.0, 2000, 32)], duration=0.002)
+    assert srv.inflight
+    fake.polls_to_finish = 2
+    st = srv.serve([req(0.0, 1000, 16)], drain=True)
+    assert [d.index for d in st.done] == [0]
+    assert all(v == {} for v in fake.live.values())
