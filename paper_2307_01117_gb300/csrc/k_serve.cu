@@ -91,6 +91,7 @@ struct ServeArgs {
   unsigned *done;            // tile counter pool
   volatile int *complete;    // host-mapped: generation of each slot's completed request
   const volatile int *stop;  // host-mapped stop word
+  const volatile int *oldest;  // host-mapped: the oldest request's slot (admission order)
   DevStatus *st;
   long long wait_ns, idle_ns;
   int T;
@@ -237,6 +238,11 @@ __global__ void __launch_bounds__(kSWarps * 32, MODE == 2 ? 1 : 8) k_serve(Serve
   unsigned long long idle_since = wave::globaltimer_ns();
   unsigned nap = 64;
   const int nslots = a.nwords * 32;
+  // half of the warps serve the oldest request first (slots are taken in
+  // admission order, so the scan from the oldest slot on follows it), the
+  // other half start anywhere and move on with every claim (processor sharing:
+  // a short request is not held behind a long one)
+  const bool fifo = (((blockIdx.x * kSWarps + wib) & 1) == 0);
   int start = (int)(((unsigned)(blockIdx.x * kSWarps + wib) * 2654435761u) % (unsigned)nslots);
   for (;;) {
     int quit = 0;
@@ -244,7 +250,14 @@ __global__ void __launch_bounds__(kSWarps * 32, MODE == 2 ? 1 : 8) k_serve(Serve
     if (__shfl_sync(tb::kFull, quit, 0)) break;
     int64_t u0 = 0;
     int cnt = 0;
-    start = start + 1 == nslots ? 0 : start + 1;
+    if (fifo) {
+      int o = 0;
+      if (lane == 0) o = *a.oldest;
+      o = __shfl_sync(tb::kFull, o, 0);
+      start = o >= 0 && o < nslots ? o : 0;
+    } else {
+      start = start + 1 == nslots ? 0 : start + 1;
+    }
     const int s = claim_unit(a, lane, start, &u0, &cnt);
     if (s == -2) continue;  // a claim past the slot's last unit: try again
     if (s < 0) {
@@ -352,6 +365,7 @@ using heat::SCtl;
 struct heat_server {
   struct Slot {
     bool used = false, complete = false, reported = false;
+    int64_t ticket = 0;  // admission order
     int64_t off = 0, len = 0, n = 0, nt = 0, done_base = 0, nseg = 0, levels = 0;
     unsigned gen = 0;
   };
@@ -374,6 +388,9 @@ struct heat_server {
   unsigned *d_done = nullptr;
   int *h_complete = nullptr, *d_complete = nullptr;  // host-mapped
   int *h_stop = nullptr, *d_stop = nullptr;          // host-mapped
+  int *h_oldest = nullptr, *d_oldest = nullptr;      // host-mapped
+  int32_t next_slot = 0;                             // slots are taken round-robin (admission order)
+  int64_t tickets = 0;                               // admission counter
   heat::DevStatus *dstat = nullptr, *hstat = nullptr;
   int host_error = HEAT_OK;
   cudaStream_t kstream = nullptr, cstream = nullptr;
@@ -451,6 +468,7 @@ int launch_serve_ep(heat_server *s) {
   a.done = s->d_done;
   a.complete = s->d_complete;
   a.stop = s->d_stop;
+  a.oldest = s->d_oldest;
   a.st = s->dstat;
   a.wait_ns = s->wait_ns;
   a.idle_ns = s->idle_ns;
@@ -478,6 +496,20 @@ int launch_serve(heat_server *s) {
   return HEAT_OK;
 }
 
+// Tell the kernel which slot holds the oldest request still in flight.
+void note_oldest(heat_server *s) {
+  int32_t best = -1;
+  int64_t t = INT64_MAX;
+  for (int32_t i = 0; i < s->S; ++i) {
+    const heat_server::Slot &sl = s->slots[i];
+    if (sl.used && !sl.reported && sl.ticket < t) {
+      t = sl.ticket;
+      best = i;
+    }
+  }
+  *(volatile int *)s->h_oldest = best < 0 ? 0 : best;
+}
+
 // Make sure the kernel runs while requests are in flight.
 int keep_running(heat_server *s) {
   if (s->in_flight == 0 || kernel_running(s)) return HEAT_OK;
@@ -501,6 +533,7 @@ void free_server(heat_server *s) {
   if (s->d_done) cudaFree(s->d_done);
   if (s->h_complete) cudaFreeHost(s->h_complete);
   if (s->h_stop) cudaFreeHost(s->h_stop);
+  if (s->h_oldest) cudaFreeHost(s->h_oldest);
   if (s->dstat) cudaFree(s->dstat);
   if (s->hstat) cudaFreeHost(s->hstat);
   if (s->kdone) cudaEventDestroy(s->kdone);
@@ -553,10 +586,12 @@ int heat_server_create(heat_server **out, int64_t capacity_points, heat_dtype dt
   if (rc == HEAT_OK &&
       (cudaHostAlloc((void **)&s->h_complete, sizeof(int) * (size_t)s->S, cudaHostAllocMapped) != cudaSuccess ||
        cudaHostAlloc((void **)&s->h_stop, sizeof(int), cudaHostAllocMapped) != cudaSuccess ||
+       cudaHostAlloc((void **)&s->h_oldest, sizeof(int), cudaHostAllocMapped) != cudaSuccess ||
        cudaHostAlloc((void **)&s->hstat, sizeof(heat::DevStatus), cudaHostAllocDefault) != cudaSuccess))
     rc = HEAT_ENOMEM;
   if (rc == HEAT_OK && (cudaHostGetDevicePointer((void **)&s->d_complete, s->h_complete, 0) != cudaSuccess ||
-                        cudaHostGetDevicePointer((void **)&s->d_stop, s->h_stop, 0) != cudaSuccess))
+                        cudaHostGetDevicePointer((void **)&s->d_stop, s->h_stop, 0) != cudaSuccess ||
+                        cudaHostGetDevicePointer((void **)&s->d_oldest, s->h_oldest, 0) != cudaSuccess))
     rc = HEAT_ECUDA;
   if (rc == HEAT_OK && (cudaStreamCreateWithFlags(&s->kstream, cudaStreamNonBlocking) != cudaSuccess ||
                         cudaStreamCreateWithFlags(&s->cstream, cudaStreamNonBlocking) != cudaSuccess ||
@@ -566,6 +601,7 @@ int heat_server_create(heat_server **out, int64_t capacity_points, heat_dtype dt
   if (rc == HEAT_OK) {
     memset(s->h_complete, 0, sizeof(int) * (size_t)s->S);
     *s->h_stop = 0;
+    *s->h_oldest = 0;
     if (cudaMemsetAsync(s->d_req, 0, sizeof(SReq) * (size_t)s->S, s->cstream) != cudaSuccess ||
         cudaMemsetAsync(s->d_ctl, 0, sizeof(SCtl) * (size_t)s->S, s->cstream) != cudaSuccess ||
         cudaMemsetAsync(s->d_live, 0, sizeof(unsigned) * (size_t)((s->S + 31) / 32), s->cstream) != cudaSuccess ||
@@ -609,11 +645,13 @@ int heat_server_submit(heat_server *s, int64_t n, double k, double dt, double dx
   if (!isfinite(r)) return HEAT_EINVAL;
   if (s->host_error != HEAT_OK) return HEAT_ESTATE;
   int32_t id = -1;
-  for (int32_t i = 0; i < s->S; ++i)
+  for (int32_t q = 0; q < s->S; ++q) {  // round-robin from the last slot taken: slot order is admission order
+    const int32_t i = (s->next_slot + q) % s->S;
     if (!s->slots[i].used) {
       id = i;
       break;
     }
+  }
   if (id < 0) return HEAT_ENOMEM;
   const int64_t len = (n + 63) / 64 * 64;
   const int64_t W = s->window - 2 * (int64_t)s->T;
@@ -671,6 +709,8 @@ int heat_server_submit(heat_server *s, int64_t n, double k, double dt, double dx
   heat_server::Slot &sl = s->slots[id];
   sl.used = true;
   sl.complete = sl.reported = false;
+  sl.ticket = s->tickets++;
+  s->next_slot = (id + 1) % s->S;
   sl.off = off;
   sl.len = len;
   sl.n = n;
@@ -681,6 +721,7 @@ int heat_server_submit(heat_server *s, int64_t n, double k, double dt, double dx
   sl.gen = gen;
   s->in_flight += 1;
   *req_id = id;
+  note_oldest(s);
   return keep_running(s);
 }
 
@@ -696,6 +737,7 @@ int heat_server_poll(heat_server *s, int32_t *done_ids, int32_t max, int32_t *co
     s->point_steps += sl.n * sl.nt;
     done_ids[(*count)++] = i;
   }
+  if (*count) note_oldest(s);
   if (s->host_error != HEAT_OK) return s->host_error;
   return keep_running(s);
 }
