@@ -544,16 +544,19 @@ class RingRunner:
         last = self.H.heat_last_run(self.h.ctx)
         form = last["form"]
         launches = max(1, last["launches"])
-        name = {"plain": "k_plain_f64" if self.w["dtype"] == "f64" else "k_plain_f32c", "persist": "k_persist",
+        # the flag-queue form at depth T > 1 runs k_queue (T-point messages)
+        name = {"plain": "k_plain_f64" if self.w["dtype"] == "f64" else "k_plain_f32c",
+                "persist": "k_queue" if last["T"] > 1 else "k_persist",
                 "tblock": "k_tblock", "cluster": "k_cluster", "persist_tb": "k_wave"}[form]
         src = {"k_plain_f64": "k_plain.cu", "k_plain_f32c": "k_plain.cu", "k_persist": "k_persist.cu",
-               "k_tblock": "k_tblock.cu", "k_cluster": "k_cluster.cu", "k_wave": "k_wave.cu"}[name]
+               "k_queue": "k_queue.cu", "k_tblock": "k_tblock.cu", "k_cluster": "k_cluster.cu",
+               "k_wave": "k_wave.cu"}[name]
         srcs = [f"paper_2307_01117_gb300/csrc/{src}", "paper_2307_01117_gb300/csrc/stencil_ops.cuh"]
-        if name in ("k_tblock", "k_cluster", "k_wave"):
+        if name in ("k_tblock", "k_cluster", "k_wave", "k_queue"):
             srcs.append("paper_2307_01117_gb300/csrc/tb_core.cuh")
-        if name in ("k_tblock", "k_wave"):
+        if name in ("k_tblock", "k_wave", "k_queue"):
             srcs.append("paper_2307_01117_gb300/csrc/dp_emul.cuh")
-        if name == "k_wave":
+        if name in ("k_wave", "k_queue"):
             srcs.append("paper_2307_01117_gb300/csrc/wave_core.cuh")
         steps_per_launch = self.nt / launches
         elem = 8.0 if self.w["dtype"] == "f64" else 4.0
@@ -561,13 +564,15 @@ class RingRunner:
         # streams the ring through HBM once per step
         # (the cluster form keeps the ring in shared memory: one read and one write per launch;
         # the persistent temporal-blocking form reads and writes the ring once per T-step level)
-        passes = {"persist": steps_per_launch, "persist_tb": -(-steps_per_launch // max(1, last["T"]))}.get(form, 1.0)
+        passes = {"persist": -(-steps_per_launch // max(1, last["T"])),
+                  "persist_tb": -(-steps_per_launch // max(1, last["T"]))}.get(form, 1.0)
         alg_bytes = 2.0 * elem * self.n * passes
         r = self.w["k"] * self.w["dt"] / (self.w["dx"] * self.w["dx"])
         return {"kernel": name, "src": srcs, "launches": launches, "launch_ms": statistics.mean(run_ms) / launches,
                 "point_steps_per_launch": self.n * steps_per_launch, "alg_bytes_per_launch": alg_bytes,
                 "form": form, "T": last["T"], "segments": last["segments"] if form != "plain" else None,
-                "emul_share": self.H.heat_get_emulation(self.h.ctx) if form in ("tblock", "persist_tb") else 0,
+                "emul_share": self.H.heat_get_emulation(self.h.ctx)
+                if form in ("tblock", "persist_tb") or name == "k_queue" else 0,
                 "r_pow2": is_pow2(r),
                 # FP64-unit operations per point-step: for r = 2^k every form but the strided
                 # temporal-blocking layout multiplies by moving the exponent on the integer pipes

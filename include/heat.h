@@ -75,7 +75,13 @@ typedef enum {
                             synchronous, unsegmented variant) */
   HEAT_FORM_PERSIST = 1, /* one persistent launch; each CTA owns a segment and
                             swaps ghost values with its neighbours through
-                            device-memory flag queues (Section 2's SPSC queues) */
+                            device-memory flag queues (Section 2's SPSC queues).
+                            Depth T: each message carries T edge values and the
+                            segment advances T steps per message (register-
+                            resident warp tiles, binary64 split between the
+                            FP64 unit and the integer pipes as in the
+                            temporal-blocking forms); T = 1: one value and one
+                            step per message */
   HEAT_FORM_TBLOCK = 2,  /* temporal blocking: T steps per register-resident tile */
   HEAT_FORM_AUTO = 3,    /* library picks (measured fastest for each range):
                             HEAT_FORM_CLUSTER for every ring the cluster form
@@ -154,23 +160,28 @@ int heat_sync(heat_ctx *c);
  * torch.cuda.Stream); NULL restores the context's own stream. */
 int heat_set_stream(heat_ctx *c, void *cuda_stream);
 
-/* Select the kernel form and, for the blocked forms (HEAT_FORM_TBLOCK,
- * HEAT_FORM_CLUSTER, HEAT_FORM_PERSIST_TB), the temporal block depth T (1..64;
+/* Select the kernel form and, for the blocked forms (HEAT_FORM_PERSIST,
+ * HEAT_FORM_TBLOCK, HEAT_FORM_CLUSTER, HEAT_FORM_PERSIST_TB), the temporal
+ * block depth T (1..64;
  * 0 = library default: 32 for HEAT_F32C; for HEAT_F64 in the temporal-blocking
  * form 24 on rings below 2^19 points (12 there when integer tiles run at an r
  * that is not a power of two), else 12 when part of the tiles run on the
  * integer pipes, else 8 below 2^22 points and 4 from 2^22 points; in the
  * cluster form 16, or 8 for rings that one cluster holds only at that depth;
- * in the persistent temporal-blocking form 32 for HEAT_F32C, for HEAT_F64 16
- * below 2^19 points, 8 from 2^19 to 2^21 and 16 from 2^21).  T is ignored by the one-step forms.
+ * in the persistent temporal-blocking and flag-queue forms 32 for HEAT_F32C,
+ * for HEAT_F64 16 below 2^19 points, 8 from 2^19 to 2^21 and 16 from 2^21).
+ * The flag-queue form runs at depth 1 when a partition is shorter than T.
+ * T is ignored by the plain form.
  * HEAT_FORM_AUTO (the default) is HEAT_FORM_CLUSTER for binary64 rings of at
  * most 6144 points and binary32 rings that one thread-block cluster holds,
  * HEAT_FORM_PERSIST_TB for binary64 rings under the exact reading from 2^18 to
  * 2^26 points, else HEAT_FORM_TBLOCK. */
 int heat_set_form(heat_ctx *c, int form, int T);
 
-/* Segmentation of the persistent forms: 0 = library default (near-equal
- * segments, one per co-resident CTA, interior boundaries on 64-point tiles);
+/* Segmentation of the persistent flag-queue form: 0 = library default
+ * (near-equal segments, one per co-resident CTA; at depth 1 interior
+ * boundaries fall on 64-point tiles, deeper every segment keeps at least T
+ * points);
  * -1 = one segment per partition of nx points, as in the paper's algorithm, when
  * np CTAs can be co-resident (else the default); n > 0 = at most n near-equal
  * segments.  The result does not depend on this choice. */

@@ -102,6 +102,9 @@ namespace heat {
 // Launchers (each queues work on c->stream and returns a heat_status).
 int run_plain(heat_ctx *c, int64_t nt);
 int run_persist(heat_ctx *c, int64_t nt);
+int run_queue(heat_ctx *c, int64_t nt, int T);
+int persist_default_T(const heat_ctx *c);
+int prepare_segments(heat_ctx *c, int S, const int64_t *bounds);
 int run_tblock(heat_ctx *c, int64_t nt);
 int tblock_default_T(const heat_ctx *c);
 unsigned tblock_emul_mask(const heat_ctx *c);

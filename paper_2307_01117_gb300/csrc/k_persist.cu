@@ -317,7 +317,19 @@ int segment_bounds(const heat_ctx *c, int want, int64_t **out) {
   return S;
 }
 
+// Default depth of the flag-queue form: the persistent temporal-blocking
+// form's (32 for binary32; binary64 16, or 8 from 2^19 to 2^21 points).
+int persist_default_T(const heat_ctx *c) { return wave_default_T(c); }
+
+// Depth T >= 2 (the default): T-point messages, T steps per message
+// (k_queue.cu); depth 1, or partitions shorter than the depth: one value per
+// message and one step, below.
 int run_persist(heat_ctx *c, int64_t nt) {
+  const int T = c->T > 0 ? c->T : persist_default_T(c);
+  if (T >= 2) {
+    const int rc = run_queue(c, nt, T);
+    if (rc != HEAT_ENOTSUP) return rc;
+  }
   const int mode = c->dtype == HEAT_F32C ? 2 : (c->arith == HEAT_ARITH_FMA ? 1 : 0);
   const int resident = mode == 0 ? max_resident<0>(c) : mode == 1 ? max_resident<1>(c) : max_resident<2>(c);
   if (resident < 1) return HEAT_ECUDA;

@@ -94,13 +94,45 @@ __device__ __forceinline__ void tile_bounds(int64_t n, int64_t ntiles, int64_t j
   hi = lo + q + (j < rem ? 1 : 0);
 }
 
+// Advance a window held in registers by `steps` (<= T) steps.  int_tile:
+// binary64 under the exact reading, compute on the integer pipes when the
+// window passes the screen; p2: for r = +-2^k the FP64-unit path moves the
+// product's exponent when the window passes the screen.
+template <int MODE, int EP>
+__device__ __forceinline__ void advance_window(typename tb::TBCx<MODE, EP>::Reg &R, int steps, double r, float rf,
+                                               bool int_tile, bool p2, const Engine &e, int lane) {
+  using P = tb::TBCx<MODE, EP>;
+  constexpr int E = P::E;
+  bool dp = true;
+  if constexpr (MODE == 0) {
+    if (int_tile || p2) {
+      bool okd = true;
+#pragma unroll
+      for (int k = 0; k < E; ++k)
+        okd &= emul::in_domain((uint64_t)__double_as_longlong(P::store(R, k)), e.dom_lo, e.dom_hi);
+      if (__all_sync(tb::kFull, okd)) {  // else the whole tile takes the plain FP64-unit steps
+        if (!int_tile)
+          for (int s = 0; s < steps; ++s) P::step_p2(R, e.p2_hi_add, e.p2_hi_xor);
+        else if (e.mx.pow2 && !e.mx.neg)
+          P::template steps_x<true, false>(R, steps, e.mx);
+        else if (e.mx.pow2)
+          P::template steps_x<true, true>(R, steps, e.mx);
+        else if (!e.mx.neg)
+          P::template steps_x<false, false>(R, steps, e.mx);
+        else
+          P::template steps_x<false, true>(R, steps, e.mx);
+        dp = false;
+      }
+    }
+  }
+  if (dp)
+    for (int s = 0; s < steps; ++s) P::step(R, lane, r, rf);
+}
+
 // Advance tile [lo, hi) of a ring of n points from src to dst by `steps`
-// (<= T) steps.  int_tile: binary64 under the exact reading, compute on the
-// integer pipes when the window passes the screen; p2: for r = +-2^k the
-// FP64-unit path moves the product's exponent when the window passes the
-// screen.  Window points past hi + T feed no stored output and are loaded as
-// zeros.  Loads bypass L1, which may still hold lines of this buffer from two
-// levels back.
+// (<= T) steps (advance_window).  Window points past hi + T feed no stored
+// output and are loaded as zeros.  Loads bypass L1, which may still hold lines
+// of this buffer from two levels back.
 template <int MODE, int EP>
 __device__ __forceinline__ void advance_tile(const typename tb::TBCx<MODE, EP>::T *src,
                                              typename tb::TBCx<MODE, EP>::T *dst, int64_t n, int64_t lo, int64_t hi,
@@ -127,30 +159,7 @@ __device__ __forceinline__ void advance_tile(const typename tb::TBCx<MODE, EP>::
     }
     P::load(R, k, v);
   }
-  bool dp = true;
-  if constexpr (MODE == 0) {
-    if (int_tile || p2) {
-      bool okd = true;
-#pragma unroll
-      for (int k = 0; k < E; ++k)
-        okd &= emul::in_domain((uint64_t)__double_as_longlong(P::store(R, k)), e.dom_lo, e.dom_hi);
-      if (__all_sync(tb::kFull, okd)) {  // else the whole tile takes the plain FP64-unit steps
-        if (!int_tile)
-          for (int s = 0; s < steps; ++s) P::step_p2(R, e.p2_hi_add, e.p2_hi_xor);
-        else if (e.mx.pow2 && !e.mx.neg)
-          P::template steps_x<true, false>(R, steps, e.mx);
-        else if (e.mx.pow2)
-          P::template steps_x<true, true>(R, steps, e.mx);
-        else if (!e.mx.neg)
-          P::template steps_x<false, false>(R, steps, e.mx);
-        else
-          P::template steps_x<false, true>(R, steps, e.mx);
-        dp = false;
-      }
-    }
-  }
-  if (dp)
-    for (int s = 0; s < steps; ++s) P::step(R, lane, r, rf);
+  advance_window<MODE, EP>(R, steps, r, rf, int_tile, p2, e, lane);
 #pragma unroll
   for (int k = 0; k < E; ++k) {
     const int idx = E * lane + k;

@@ -17,9 +17,9 @@ from paper_2307_01117_gb300 import workloads
 
 pytestmark = pytest.mark.gpu
 
-FORMS_F64 = [("plain", 0), ("persist", 0), ("tblock", 1), ("tblock", 4), ("tblock", 7), ("tblock", 64),
+FORMS_F64 = [("plain", 0), ("persist", 0), ("persist", 1), ("persist", 5), ("persist", 64), ("tblock", 1), ("tblock", 4), ("tblock", 7), ("tblock", 64),
              ("persist_tb", 1), ("persist_tb", 4), ("persist_tb", 13)]
-FORMS_F32C = [("plain", 0), ("persist", 0), ("tblock", 1), ("tblock", 8), ("tblock", 13), ("tblock", 64),
+FORMS_F32C = [("plain", 0), ("persist", 0), ("persist", 1), ("persist", 13), ("tblock", 1), ("tblock", 8), ("tblock", 13), ("tblock", 64),
               ("persist_tb", 8), ("persist_tb", 32)]
 
 
@@ -109,9 +109,14 @@ def test_f32c_bitwise(form, T, n):
     u0 = workloads.uniform(n, 5 + n, -1, 1)
     u32 = u0.astype(np.float32)
     for nt, r in [(1, 0.5), (13, 0.3), (40, 0.25)]:
+        with H.Heat(n, 1, r, 1.0, 1.0, dtype="f32c", form=form, T=T) as h:
+            got = h.set(u0).run(nt).get()
+            last_T = H.heat_last_run(h.ctx)["T"]
         Tb = T if form in ("tblock", "persist_tb") else 1
+        if form == "persist":   # depth T (library default 32), or 1 on rings shorter than T
+            assert last_T in (1, T or 32), last_T
+            Tb = last_T
         ref = oracle.run_f32c(u32, np.float32(r), nt, max(Tb, 1)).astype(np.float64)
-        got = run_gpu(u0, 1, r, nt, form, T, dtype="f32c")
         assert np.array_equal(got, ref), (n, nt, r)
 
 
