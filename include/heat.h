@@ -168,8 +168,9 @@ int heat_set_stream(heat_ctx *c, void *cuda_stream);
  * that is not a power of two), else 12 when part of the tiles run on the
  * integer pipes, else 8 below 2^22 points and 4 from 2^22 points; in the
  * cluster form 16, or 8 for rings that one cluster holds only at that depth;
- * in the persistent temporal-blocking and flag-queue forms 32 for HEAT_F32C,
- * for HEAT_F64 16 below 2^19 points, 8 from 2^19 to 2^21 and 16 from 2^21).
+ * in the persistent temporal-blocking form 32 for HEAT_F32C, for HEAT_F64 16
+ * below 2^19 points, 12 from 2^19 to 2^21 and 16 from 2^21; in the flag-queue
+ * form 32 for HEAT_F32C, for HEAT_F64 8 below 2^21 points and 16 from 2^21).
  * The flag-queue form runs at depth 1 when a partition is shorter than T.
  * T is ignored by the plain form.
  * HEAT_FORM_AUTO (the default) is HEAT_FORM_CLUSTER for binary64 rings of at

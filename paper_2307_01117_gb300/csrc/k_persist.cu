@@ -317,9 +317,15 @@ int segment_bounds(const heat_ctx *c, int want, int64_t **out) {
   return S;
 }
 
-// Default depth of the flag-queue form: the persistent temporal-blocking
-// form's (32 for binary32; binary64 16, or 8 from 2^19 to 2^21 points).
-int persist_default_T(const heat_ctx *c) { return wave_default_T(c); }
+// Default depth of the flag-queue form: 32 for binary32; binary64 8 below 2^21
+// points, where a segment holds few tiles per block (10^6 points, r = 1/4:
+// 234.6 GLUP/s at 8, 209.3 at 4, 162.0 at 12), else 16 (2^25 points: 307.3 at
+// 16, 302.7 at 12; deeper blocks leave the integer routines' domain at
+// r = 0.3).
+int persist_default_T(const heat_ctx *c) {
+  if (c->dtype == HEAT_F32C) return 32;
+  return c->geo.N < (1LL << 21) ? 8 : 16;
+}
 
 // Depth T >= 2 (the default): T-point messages, T steps per message
 // (k_queue.cu); depth 1, or partitions shorter than the depth: one value per

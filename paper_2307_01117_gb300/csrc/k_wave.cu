@@ -40,7 +40,13 @@ namespace {
 
 constexpr int kWaveWarps = 4;  // warps per CTA
 // window chooser: tiles per level per SM the widest window must still give
-constexpr int kWaveTilesPerLevelPerSM = 48;
+constexpr int kWaveTilesPerLevelPerSM = 24;
+// resident warps per tile of a level, in percent: on mid-size rings a unit's
+// latency chains the levels (every warp holds a distinct part of the ring), so
+// fewer, faster warps on wider windows beat a full SM on narrow ones (10^6
+// points, T = 12: 6 CTAs per SM on 256-point windows 295.6 GLUP/s, 9 CTAs per
+// SM on 128-point windows at T = 8 281.3)
+constexpr int kWaveWarpsPerTilePct = 85;
 
 struct WaveArgs {
   void *buf0, *buf1;
@@ -119,6 +125,11 @@ int launch_wave_ep(heat_ctx *c, WaveArgs a) {
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_wave<MODE, EP>, kWaveWarps * 32, 0) != cudaSuccess ||
       per_sm < 1)
     return HEAT_ECUDA;
+  // CTAs per SM: as many as fit, or the nearest count giving about
+  // kWaveWarpsPerTilePct warps per 100 tiles of a level when that is fewer
+  const int64_t per_sm_cap = (a.ntiles * kWaveWarpsPerTilePct / 100 + (int64_t)kWaveWarps * c->sms / 2) /
+                             ((int64_t)kWaveWarps * c->sms);
+  if (per_sm_cap >= 1 && per_sm_cap < per_sm) per_sm = (int)per_sm_cap;
   int64_t grid = (a.units + kWaveWarps - 1) / kWaveWarps;
   const int64_t cap = (int64_t)per_sm * c->sms;
   if (grid > cap) grid = cap;
@@ -172,13 +183,14 @@ void free_wave(heat_ctx *c) {
 // Default depth: binary32 pairs 32 steps per pass.  Binary64: 16 below 2^19
 // points, where the chain of levels (each waits on the one before) is the
 // bound and fewer levels pay more than the narrower tiles' halo costs (2^18
-// points: 171.8 GLUP/s at 16, 169.7 at 12, 159.9 at 8); 8 from 2^19 to 2^21,
-// where the halo of the narrowest window weighs most (10^6 points: 281.4 at 8,
-// 269.8 at 12, 253.3 at 16); 16 above (2^22 points: 317.0 at 16, 309.6 at 12).
+// points, r = 1/4: 222.5 GLUP/s at 16, 214.2 at 12, 201.0 at 8); 12 from 2^19
+// to 2^21 (10^6 points: 295.6 at 12, 295.3 at 10, 292.9 at 16, 280.7 at 8;
+// r = 0.3: 224.2, 217.8, 224.3, 185.1); 16 above (2^22 points: 316.8 at 16,
+// 309.5 at 12).
 int wave_default_T(const heat_ctx *c) {
   if (c->dtype == HEAT_F32C) return 32;
   if (c->geo.N < (1LL << 19)) return 16;
-  return c->geo.N < (1LL << 21) ? 8 : 16;
+  return c->geo.N < (1LL << 21) ? 12 : 16;
 }
 
 // HEAT_FORM_AUTO takes this form for binary64 rings under the exact reading

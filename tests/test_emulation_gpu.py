@@ -146,10 +146,10 @@ def test_two_engine_split_on_a_large_ring_is_bitwise_the_oracle(k):
 def test_library_default_on_mid_size_rings_is_bitwise_the_oracle(k):
     """The library's default from 2^18 to 2^26 binary64 points: one
     dependency-driven launch (persistent temporal blocking, warp tiles split
-    between the FP64 unit and the integer pipes), depth 16 below 2^19 points, 8
+    between the FP64 unit and the integer pipes), depth 16 below 2^19 points, 12
     from 2^19 to 2^21 and 16 above, element by element against the oracle with
     a partial last block."""
-    for n, T in [(1 << 18, 16), (1 << 19, 8), (10**6, 8), (1 << 22, 16)]:
+    for n, T in [(1 << 18, 16), (1 << 19, 12), (10**6, 12), (1 << 22, 16)]:
         u0 = workloads.uniform_plus_mode(n, seed=12, m=5)
         with H.Heat(n // 4, 4, k, 1.0, 1.0) as h:
             got = h.set(u0).run(3 * T + 5).get()
