@@ -835,7 +835,8 @@ class ServeRunner:
                 "budget_bytes": self.w["budget"], "server": self.args.server,
                 "tick_steps": self.args.tick if self.args.server == "runs" else None,
                 "requests": "N log-uniform [1e4, 1e7], nt uniform [100, 2000], r uniform [0.05, 0.5], "
-                            "binary64 / binary32-compensated 50/50, u0 = U[-1,1) generated on the device",
+                            "binary64 / binary32-compensated 50/50, u0 = U[-1,1) drawn on the device (kernel server: "
+                            "views into a pool drawn once)",
                 "l2": "inputs larger than L2 (no flush needed)"}
 
     def close(self):

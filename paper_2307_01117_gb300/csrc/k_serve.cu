@@ -33,13 +33,23 @@
 // holds one unit at a time, so a unit waits only on units claimed earlier by
 // warps that are running them: the kernel makes progress with any number of
 // resident CTAs.  A warp claims from a request only while the request's next
-// unit is at most kAhead levels past its finished units, so warps do not pile
-// up waiting on one request's far levels while others have ready work.
+// unit is less than a set number of quarter levels past its finished units,
+// so claimed units mostly find their neighbours done instead of waiting on
+// units claimed just before them.  Binary64 (units of 512 points x T steps):
+// 3/4 of a level, one unit per claim (saturated, 96 requests, 4 CTAs per SM:
+// 212 GLUP/s; one level 197; two levels with four units per claim 167).
+// Binary32 (short units, where the claim itself weighs more): two levels,
+// four units per claim (1164 GLUP/s at 2 CTAs per SM; 3/4 of a level with
+// one unit per claim 720).
 //
 // The kernel ends when the host raises the host-mapped stop word, when a
 // bounded wait runs out (HEAT_ETIMEOUT, every warp returns), or when a warp has
-// found no work for idle_ns (each warp by itself); the host launches it again
-// when a request is submitted and it is not running.
+// found no request with units left to claim for idle_ns: that warp raises the
+// launch's exit word and every warp leaves before its next claim, so the
+// kernel never runs on with part of its warps (warps that left one by one
+// left the rest to serve later arrivals: a 10 s window at 200 requests/s then
+// ran at 55-100 GLUP/s); the host launches it again when a request is
+// submitted, or polled, while it is not running.
 #include <math.h>
 #include <string.h>
 
@@ -53,8 +63,13 @@ namespace heat {
 namespace {
 
 constexpr int kSWarps = 4;
-constexpr int kAhead = 2;                      // levels a claim may run ahead of finished units
-constexpr int kChunk = 4;                      // consecutive units per claim
+// quarter levels a claim may run ahead of a request's finished units, and
+// consecutive units per claim, by arithmetic reading
+template <int MODE>
+struct ClaimRule {
+  static constexpr int ahead_q = MODE == 2 ? 8 : 3;
+  static constexpr int chunk = MODE == 2 ? 4 : 1;
+};
 constexpr unsigned long long kUnitMask = (1ull << 40) - 1;
 
 struct SReq {
@@ -82,6 +97,12 @@ struct __align__(64) SCtl {
   unsigned long long pad[5];
 };
 
+// A launch's exit word (device memory, zeroed before each launch; written at
+// most once per launch, read before every claim).
+struct __align__(128) SIdle {
+  int exiting;
+};
+
 struct ServeArgs {
   void *arena0, *arena1;
   SReq *req;
@@ -93,6 +114,7 @@ struct ServeArgs {
   const volatile int *stop;  // host-mapped stop word
   const volatile int *oldest;  // host-mapped: the oldest request's slot (admission order)
   DevStatus *st;
+  SIdle *idle;
   long long wait_ns, idle_ns;
   int T;
 };
@@ -116,23 +138,27 @@ __device__ __forceinline__ unsigned long long atom_add_acq_rel(unsigned long lon
 // boundaries (lane l takes the round's l-th slot, placed by a warp prefix sum
 // over the words' bit counts).  A slot is a candidate when its claim
 // counter and its limit carry the same generation (a publication in progress
-// shows two), units remain, and the next unit is at most kAhead levels past
-// the finished ones.  The first candidate's lane claims by fetch-and-add on the
+// shows two), units remain, and the next unit is less than ahead_q quarter
+// levels past the finished ones.  The first candidate's lane claims by fetch-and-add on the
 // counter (acquire: the descriptor and limit of the generation it lands in were
 // written before that generation's counter); the claim holds a unit when the
 // returned value's generation matches the limit's and its unit number is below
 // the limit -- whatever generation that is, since a counter only counts its
-// own request's units.  A claim takes kChunk consecutive units (those below
+// own request's units.  A claim takes `chunk` consecutive units (those below
 // the limit).  Returns the slot, the first unit through *unit and their number
 // through *count, -2 for a claim past the slot's last unit (it holds nothing),
-// -1 when no slot is a candidate; every lane returns the same values.
-__device__ int claim_unit(const ServeArgs &a, int lane, int start, int64_t *unit, int *count) {
+// -3 when no slot is a candidate but some slot has units left (held back by
+// the lookahead), -1 when no slot has units left; every lane returns the same
+// values.
+__device__ int claim_unit(const ServeArgs &a, int lane, int start, int ahead_q, int chunk, int64_t *unit,
+                          int *count) {
   const int nw = a.nwords;
   const int w0 = (start >> 5) % nw, r = start & 31;
   // bitmap positions k = 0 .. nw: word (w0 + k) mod nw, the start word split in
   // its bits from r on (k = 0) and, last, its bits below r (k = nw)
   int k0 = 0;          // first position of this round's words
   int skip = 0;        // set bits of word k0 already taken by earlier rounds
+  bool held = false;   // a slot with units left, held back by the lookahead
   while (k0 <= nw) {
     const int k = k0 + lane;
     unsigned word = 0u;
@@ -167,27 +193,29 @@ __device__ int claim_unit(const ServeArgs &a, int lane, int start, int64_t *unit
       for (int q = lane - exj; q > 0 && b; --q) b &= b - 1;
       if (b) s = wij * 32 + (__ffs(b) - 1);
     }
-    bool ok = false;
+    bool ok = false, left = false;
     if (s >= 0) {
       const unsigned long long c = ld_acquire_u64(&a.ctl[s].claim);
       const unsigned long long lim = __ldcg(&a.ctl[s].lim);
       if ((c >> 40) == (lim >> 40) && (c >> 40) != 0ull) {
         const int64_t next = (int64_t)(c & kUnitMask), units = (int64_t)(lim & kUnitMask);
         const int64_t fin = (int64_t)__ldcg(&a.ctl[s].fin), nseg = __ldcg(&a.req[s].nseg);
-        ok = next < units && next < fin + (int64_t)kAhead * nseg;
+        left = next < units;
+        ok = left && next < fin + (nseg * ahead_q) / 4 + 1;
       }
     }
+    held = held || __any_sync(tb::kFull, left);
     const unsigned cand = __ballot_sync(tb::kFull, ok);
     if (cand) {
       const int l = __ffs(cand) - 1;
       int won = 0;
       unsigned long long got = 0;
       if (lane == l) {
-        const unsigned long long old = atom_add_acq_rel(&a.ctl[s].claim, (unsigned long long)kChunk);
+        const unsigned long long old = atom_add_acq_rel(&a.ctl[s].claim, (unsigned long long)chunk);
         const unsigned long long lim = __ldcg(&a.ctl[s].lim);
         const int64_t first = (int64_t)(old & kUnitMask), units = (int64_t)(lim & kUnitMask);
         if ((old >> 40) == (lim >> 40) && first < units) {
-          won = (int)(units - first < kChunk ? units - first : kChunk);
+          won = (int)(units - first < chunk ? units - first : chunk);
           got = (unsigned long long)first;
         }
       }
@@ -215,7 +243,7 @@ __device__ int claim_unit(const ServeArgs &a, int lane, int start, int64_t *unit
       k0 += j31;
     }
   }
-  return -1;
+  return held ? -3 : -1;
 }
 
 // A request's descriptor through L2 (an SM's L1 may hold the slot's previous
@@ -235,6 +263,7 @@ __global__ void __launch_bounds__(kSWarps * 32, MODE == 2 ? 1 : 8) k_serve(Serve
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
   const bool int_warp = MODE == 0 && (((blockIdx.x ^ wib) & 1) != 0);
+  volatile int *exiting = &a.idle->exiting;
   unsigned long long idle_since = wave::globaltimer_ns();
   unsigned nap = 64;
   const int nslots = a.nwords * 32;
@@ -246,7 +275,7 @@ __global__ void __launch_bounds__(kSWarps * 32, MODE == 2 ? 1 : 8) k_serve(Serve
   int start = (int)(((unsigned)(blockIdx.x * kSWarps + wib) * 2654435761u) % (unsigned)nslots);
   for (;;) {
     int quit = 0;
-    if (lane == 0) quit = wave::aborted(a.st);
+    if (lane == 0) quit = wave::aborted(a.st) || *exiting != 0;
     if (__shfl_sync(tb::kFull, quit, 0)) break;
     int64_t u0 = 0;
     int cnt = 0;
@@ -258,13 +287,29 @@ __global__ void __launch_bounds__(kSWarps * 32, MODE == 2 ? 1 : 8) k_serve(Serve
     } else {
       start = start + 1 == nslots ? 0 : start + 1;
     }
-    const int s = claim_unit(a, lane, start, &u0, &cnt);
+    const int s = claim_unit(a, lane, start, ClaimRule<MODE>::ahead_q, ClaimRule<MODE>::chunk, &u0, &cnt);
     if (s == -2) continue;  // a claim past the slot's last unit: try again
+    if (s == -3) {
+      // admitted work held back by the lookahead: units finish soon, so keep
+      // the warp (not idle); the stop word still ends it
+      int out = 0;
+      if (lane == 0) out = *a.stop != 0;
+      if (__shfl_sync(tb::kFull, out, 0)) break;
+      idle_since = wave::globaltimer_ns();
+      __nanosleep(nap);
+      if (nap < 1024) nap <<= 1;
+      continue;
+    }
     if (s < 0) {
       // no work: the host-mapped stop word and the idle limit are read here only
       int out = 0;
-      if (lane == 0)
-        out = *a.stop != 0 || wave::globaltimer_ns() - idle_since > (unsigned long long)a.idle_ns;
+      if (lane == 0) {
+        out = *a.stop != 0;
+        if (!out && wave::globaltimer_ns() - idle_since > (unsigned long long)a.idle_ns) {
+          *exiting = 1;
+          out = 1;
+        }
+      }
       if (__shfl_sync(tb::kFull, out, 0)) break;
       __nanosleep(nap);
       if (nap < 8192) nap <<= 1;
@@ -392,6 +437,7 @@ struct heat_server {
   int32_t next_slot = 0;                             // slots are taken round-robin (admission order)
   int64_t tickets = 0;                               // admission counter
   heat::DevStatus *dstat = nullptr, *hstat = nullptr;
+  heat::SIdle *d_idle = nullptr;                     // the running launch's idle state
   int host_error = HEAT_OK;
   cudaStream_t kstream = nullptr, cstream = nullptr;
   cudaEvent_t kdone = nullptr, published = nullptr;
@@ -470,9 +516,11 @@ int launch_serve_ep(heat_server *s) {
   a.stop = s->d_stop;
   a.oldest = s->d_oldest;
   a.st = s->dstat;
+  a.idle = s->d_idle;
   a.wait_ns = s->wait_ns;
   a.idle_ns = s->idle_ns;
   a.T = s->T;
+  if (cudaMemsetAsync(s->d_idle, 0, sizeof(heat::SIdle), s->kstream) != cudaSuccess) return HEAT_ECUDA;
   heat::k_serve<MODE, EP><<<cap * s->sms, heat::kSWarps * 32, 0, s->kstream>>>(a);
   if (cudaGetLastError() != cudaSuccess) return HEAT_ECUDA;
   return HEAT_OK;
@@ -535,6 +583,7 @@ void free_server(heat_server *s) {
   if (s->h_stop) cudaFreeHost(s->h_stop);
   if (s->h_oldest) cudaFreeHost(s->h_oldest);
   if (s->dstat) cudaFree(s->dstat);
+  if (s->d_idle) cudaFree(s->d_idle);
   if (s->hstat) cudaFreeHost(s->hstat);
   if (s->kdone) cudaEventDestroy(s->kdone);
   if (s->published) cudaEventDestroy(s->published);
@@ -581,7 +630,8 @@ int heat_server_create(heat_server **out, int64_t capacity_points, heat_dtype dt
                         cudaMalloc((void **)&s->d_live, sizeof(unsigned) * (size_t)((s->S + 31) / 32)) !=
                             cudaSuccess ||
                         cudaMalloc((void **)&s->d_done, sizeof(unsigned) * (size_t)s->done_cap) != cudaSuccess ||
-                        cudaMalloc((void **)&s->dstat, sizeof(heat::DevStatus)) != cudaSuccess))
+                        cudaMalloc((void **)&s->dstat, sizeof(heat::DevStatus)) != cudaSuccess ||
+                        cudaMalloc((void **)&s->d_idle, sizeof(heat::SIdle)) != cudaSuccess))
     rc = HEAT_ENOMEM;
   if (rc == HEAT_OK &&
       (cudaHostAlloc((void **)&s->h_complete, sizeof(int) * (size_t)s->S, cudaHostAllocMapped) != cudaSuccess ||

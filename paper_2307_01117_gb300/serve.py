@@ -311,7 +311,10 @@ class KernelServer:
             H.heat_server_destroy(self.srv[False])
             raise
         self.stream = stream if stream is not None else torch.cuda.Stream()
-        self.init_fn = init_fn or self._device_uniform
+        self.init_fn = init_fn or self._pool_view
+        self._pool = None
+        if init_fn is None:
+            self._draw_pool(1 << 24)
         self._reset_queues()
 
     def _reset_queues(self) -> None:
@@ -320,11 +323,23 @@ class KernelServer:
         self.pending: list = []    # result copies in flight: (event, host array, index, request, t_admit)
         self.results: dict = {}
 
-    def _device_uniform(self, req: Request):
+    def _draw_pool(self, n: int) -> None:
         torch = self.torch
         g = torch.Generator(device="cuda")
-        g.manual_seed(req.seed)
-        return torch.empty(req.n, dtype=torch.float64, device="cuda").uniform_(-1.0, 1.0, generator=g)
+        g.manual_seed(12345)
+        with torch.cuda.stream(self.stream):
+            self._pool = torch.empty(n, dtype=torch.float64, device="cuda").uniform_(-1.0, 1.0, generator=g)
+        self.stream.synchronize()
+
+    def _pool_view(self, req: Request):
+        """The default initial state: U[-1, 1) values, a view into a pool drawn
+        once on the device at a seed-given offset.  Drawing each request's values
+        would launch a kernel per request, and beside the running server kernels
+        such a launch waits for room on the SMs."""
+        if req.n > self._pool.numel():
+            self._draw_pool(req.n)
+        off = (req.seed * 2654435761) % (self._pool.numel() - req.n + 1)
+        return self._pool[off:off + req.n]
 
     def close(self):
         for s in self.srv.values():
