@@ -100,8 +100,8 @@ def make_server(monkeypatch, cap_points, tick_steps=16, lookahead=64, tick_s=0.0
 READY = types.SimpleNamespace(query=lambda: True)
 
 
-def req(t, n, nt, f32c=False):
-    return Request(t_arrive=t, n=n, nt=nt, r=0.25, f32c=f32c, seed=0)
+def req(t, n, nt, f32c=False, seed=0):
+    return Request(t_arrive=t, n=n, nt=nt, r=0.25, f32c=f32c, seed=seed)
 
 
 def test_requests_wait_for_space_and_all_complete(monkeypatch):
@@ -292,3 +292,21 @@ def test_kernel_server_window_finishes_the_last_windows_requests(monkeypatch):
     st = srv.serve([req(0.0, 1000, 16)], drain=True)
     assert [d.index for d in st.done] == [0]
     assert all(v == {} for v in fake.live.values())
+
+
+def test_kernel_server_default_inputs_are_pool_views():
+    """The default initial state of a request is a view into one pool, at an
+    offset set by the request's seed: no kernel launch per request, the same
+    values for the same seed, always inside the pool."""
+    import torch
+    srv = object.__new__(serve.KernelServer)
+    srv._pool = torch.arange(1000, dtype=torch.float64)
+    for seed in range(50):
+        for n in (1, 17, 999, 1000):
+            v = srv._pool_view(req(0.0, n, 10, seed=seed))
+            assert v.numel() == n and v.data_ptr() >= srv._pool.data_ptr()
+            off = int(v[0].item())
+            assert 0 <= off <= 1000 - n and torch.equal(v, srv._pool[off:off + n])
+            assert torch.equal(v, srv._pool_view(req(0.0, n, 10, seed=seed)))
+    offs = {int(srv._pool_view(req(0.0, 10, 10, seed=s))[0].item()) for s in range(50)}
+    assert len(offs) > 40
