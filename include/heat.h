@@ -416,10 +416,14 @@ int heat_batch_info(const heat_batch *b, int32_t *live_rings, int64_t *largest_f
  * running kernel at once: no launch boundary, no host tick.  A request's result
  * is bitwise the one heat_run gives for it alone (binary64) or the one the
  * temporal-blocking form gives with the server's block depth (HEAT_F32C).
- * The server kernel ends by itself after `idle_ns` without any admitted work;
- * heat_server_submit starts it again.  While it runs, a device-wide
- * synchronisation (cudaDeviceSynchronize) waits for it to end: synchronise
- * streams instead.  The paper has no serving layer; this is the library's (it
+ * The server kernel ends by itself, all of its warps together, once a warp
+ * has found no admitted request with units left for `idle_ns`;
+ * heat_server_submit (or heat_server_poll, while requests are in flight)
+ * starts it again.  The running kernel fills most of each SM, so work the
+ * caller launches beside it waits for room: the initial states passed to
+ * heat_server_submit should be ready before the call, not computed by a
+ * kernel per request.  While it runs, a device-wide synchronisation
+ * (cudaDeviceSynchronize) waits for it to end: synchronise streams instead.  The paper has no serving layer; this is the library's (it
  * serves the paper's problem).
  * ------------------------------------------------------------------------- */
 typedef struct heat_server heat_server; /* opaque, library-owned */
